@@ -1,0 +1,87 @@
+"""Seeded synthetic inputs shared by the product path, the tests and the benchmark.
+
+This module holds no arithmetic of the method: only point clouds drawn from numpy's
+PCG64 generator, the parameter sets of the workloads, and random vectors/values used as
+inputs.  Workloads (uniform points in the unit cube as in the paper's multiplication
+benchmark, Sec. 5.1; points on the unit sphere as a stand-in for the 3D scan of
+Sec. 5.3):
+
+  matern32_2d_4096    N=4096 uniform [0,1]^2, Matern-3/2, ell=0.2, nugget 1e-3, q=2,
+                      leaf 16, eta=1.25, tau=1e-10; C = P_S(A A) in FP64.
+  matern12_3d_1m      N=2^20 uniform [0,1]^3, Matern-1/2, ell=0.1, q=3, leaf 32,
+                      eta=1.0, tau=1e-8; FP64 vs mixed precision.
+  matern52_sphere     N=2^18 on the unit sphere, Matern-5/2, ell=0.3, nugget 1e-2, q=2,
+                      leaf 16, eta=1.25; A^{1/2} (25 Newton-Schulz steps), exp(-A).
+  matern32_2d_batch   256 matrices, N log-uniform in [2^10, 2^16], uniform [0,1]^2,
+                      Matern-3/2, ell ~ U[0.05, 0.5], q=2, leaf 16, eta=1.25.
+  matern32_3d_grad    N=2^20 uniform [0,1]^3, Matern-3/2, ell=0.15, q=2, 10 NS steps,
+                      gradient checked at N=4096.
+"""
+from dataclasses import dataclass, replace
+
+import numpy as np
+
+
+@dataclass(frozen=True)
+class Workload:
+    name: str
+    seed: int
+    n: int
+    d: int
+    domain: str          # "cube" or "sphere"
+    nu: float
+    ell: float
+    nugget: float
+    q: int
+    leaf: int
+    eta: float
+    tau: float
+    scale_by_n: bool = True   # kernel scaled by 1/N as in Sec. 5
+
+    @property
+    def scale(self):
+        return 1.0 / self.n if self.scale_by_n else 1.0
+
+    def with_n(self, n):
+        return replace(self, n=n)
+
+
+WORKLOADS = {
+    "matern32_2d_4096": Workload("matern32_2d_4096", 1, 4096, 2, "cube", 1.5, 0.2, 1e-3, 2, 16, 1.25, 1e-10),
+    "matern12_3d_1m": Workload("matern12_3d_1m", 2, 1 << 20, 3, "cube", 0.5, 0.1, 0.0, 3, 32, 1.0, 1e-8),
+    "matern52_sphere": Workload("matern52_sphere", 3, 1 << 18, 3, "sphere", 2.5, 0.3, 1e-2, 2, 16, 1.25, 0.0),
+    "matern32_2d_batch": Workload("matern32_2d_batch", 4, 0, 2, "cube", 1.5, 0.0, 0.0, 2, 16, 1.25, 0.0),
+    "matern32_3d_grad": Workload("matern32_3d_grad", 5, 1 << 20, 3, "cube", 1.5, 0.15, 0.0, 2, 16, 1.25, 0.0),
+}
+
+
+def points(w, n=None, seed=None):
+    """n points of the workload's domain from PCG64(seed)."""
+    n = w.n if n is None else n
+    rng = np.random.Generator(np.random.PCG64(w.seed if seed is None else seed))
+    if w.domain == "cube":
+        return rng.random((n, w.d))
+    if w.domain == "sphere":
+        g = rng.standard_normal((n, w.d))
+        return g / np.linalg.norm(g, axis=1, keepdims=True)
+    raise ValueError(w.domain)
+
+
+def batch_workloads(count=256, seed=4, nmin_log2=10, nmax_log2=16):
+    """The batched workload: N = floor(2^U[10,16]), ell ~ U[0.05, 0.5]."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    ns = np.floor(2.0 ** rng.uniform(nmin_log2, nmax_log2, size=count)).astype(np.int64)
+    ells = rng.uniform(0.05, 0.5, size=count)
+    base = WORKLOADS["matern32_2d_batch"]
+    return [replace(base, name="%s_%d" % (base.name, i), seed=1000 + i, n=int(n), ell=float(l))
+            for i, (n, l) in enumerate(zip(ns, ells))]
+
+
+def random_vector(n, seed):
+    rng = np.random.Generator(np.random.PCG64(seed))
+    return rng.standard_normal(n)
+
+
+def random_values(count, seed, lo=-1.0, hi=1.0):
+    rng = np.random.Generator(np.random.PCG64(seed))
+    return rng.uniform(lo, hi, size=count)
