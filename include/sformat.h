@@ -1,0 +1,156 @@
+/*
+ * sformat.h -- C ABI of the GB300 samplet S-format algebra library (libsformat.so).
+ *
+ * The library computes with samplet-compressed kernel matrices in the S-format of
+ * Harbrecht, Multerer, Schenk, Schwab, "Multiresolution kernel matrix algebra"
+ * (arXiv 2211.11681): matrices in samplet coordinates, stored only on a block pattern S of
+ * cluster pairs (nu, nu') of one cluster tree (Sec. 3.3, Thm. (S-compression), Eq. (cutoff)).
+ *
+ * Storage ("block-CSR"): the matrix dimension N is split into n_clusters consecutive row
+ * ranges, cluster nu owning rows block_offset[nu] .. block_offset[nu+1]-1 (its samplets;
+ * the root cluster also owns the root scaling functions).  The pattern lists, for every
+ * block row nu, the block columns colidx[rowptr[nu] .. rowptr[nu+1]-1] in strictly
+ * increasing order.  Block k = (nu, colidx[k]) holds bsize(nu) x bsize(colidx[k]) entries,
+ * row-major; the blocks are packed one after the other in pattern order, so the value
+ * buffer of a matrix on pattern S holds s_pattern_nnz(S) entries and block k starts at
+ * entry s_pattern_block_offsets(S)[k].
+ *
+ * Value buffers are DEVICE pointers owned by the caller; the library never frees them.
+ * Their element type is double for S_FP64 and S_FP64_DF (and for s_add/s_funm with
+ * S_FP64), float for S_FP32 and S_BF16X3.  Handles are owned by the library: destroy
+ * them explicitly.  Every call returns an s_status; on error nothing is freed and output
+ * buffers are unspecified.  Calls that take a stream enqueue asynchronously on it (a
+ * cudaStream_t passed as void*, NULL = legacy default stream); a device fault surfaces as
+ * S_ERR_CUDA at the next call that synchronises.  s_last_error() returns a
+ * thread-local message for the last failing call of the calling thread.
+ *
+ * All operands of one call must come from the same cluster tree: patterns carry a hash
+ * of (block_offset, level), and mismatches return S_ERR_MISMATCH.
+ */
+#ifndef SFORMAT_H
+#define SFORMAT_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct s_pattern_t* s_pattern;
+typedef struct s_plan_t* s_plan;
+
+typedef enum {
+  S_OK = 0,
+  S_ERR_ARG = -1,           /* bad argument (null pointer, size, enum)               */
+  S_ERR_PATTERN = -2,       /* malformed pattern arrays                               */
+  S_ERR_MISMATCH = -3,      /* operands from different trees / incompatible patterns  */
+  S_ERR_NOMEM = -4,         /* device or host allocation failed                       */
+  S_ERR_CUDA = -5,          /* a CUDA call failed; see s_last_error()                 */
+  S_ERR_NOT_CONVERGED = -6, /* Newton-Schulz residual grew over two consecutive steps */
+  S_ERR_TIMEOUT = -7        /* a bounded device-side wait ran out                     */
+} s_status;
+
+/* Arithmetic of a product.
+ *   S_FP64     double in, double out, double multiply-add.
+ *   S_FP64_DF  double in, double out; each operand split into a pair of floats
+ *              (hi + lo) and the products formed in float-pair arithmetic with float
+ *              error-free transformations; about 2^-44 relative per operation.
+ *   S_FP32     float in, float out, float multiply-add.
+ *   S_BF16X3   float in, float out; each operand split into three bfloat16 parts,
+ *              the six leading cross products on the tensor cores, float accumulate. */
+typedef enum { S_FP64 = 0, S_FP32 = 1, S_BF16X3 = 2, S_FP64_DF = 3 } s_prec;
+
+typedef enum { S_SQRT = 0, S_EXP = 1, S_EXP_NEG = 2 } s_fn;
+
+/* ---- patterns ------------------------------------------------------------------------ */
+
+/* Create a pattern from host arrays (copied; the caller keeps ownership).
+ *   n_clusters   number of clusters (block rows), >= 1.
+ *   block_offset n_clusters+1 row offsets, block_offset[0] = 0, non-decreasing; a cluster
+ *                may own zero rows, in which case its block row and column must be empty.
+ *   level        n_clusters cluster levels (root = 0), used only for the tree hash.
+ *   rowptr       n_clusters+1 block-row pointers, rowptr[0] = 0, non-decreasing.
+ *   colidx       rowptr[n_clusters] block columns, strictly increasing within a row, in
+ *                [0, n_clusters).
+ * Validates every array (S_ERR_PATTERN on a violation) and uploads it to the current
+ * device.  The pattern of Eq. (cutoff) is one instance; any block pattern is accepted. */
+s_status s_pattern_create(int32_t n_clusters, const int64_t* block_offset, const int32_t* level,
+                          const int64_t* rowptr, const int32_t* colidx, s_pattern* out);
+s_status s_pattern_destroy(s_pattern p);
+/* Number of stored entries (length of a value buffer), or -1 for a NULL pattern. */
+int64_t s_pattern_nnz(s_pattern p);
+/* Number of blocks, or -1. */
+int64_t s_pattern_nblocks(s_pattern p);
+/* Copies the nblocks+1 entry offsets of the blocks into host memory `out`. */
+s_status s_pattern_block_offsets(s_pattern p, int64_t* out);
+
+/* ---- masked product, Eq. (product) of Thm. (product), Sec. 4.1 ---------------------- */
+
+/* Symbolic phase of C = P_{S_C}(A B): checks that the three patterns share one tree,
+ * builds the intersection work list of S_C x (S_A, S_B) on the device and counts the
+ * block triples (nu, lambda, nu') and useful flops sum 2 n_nu n_lambda n_nu'.  The plan
+ * keeps references to the patterns, which must outlive it. */
+s_status s_plan_create(s_pattern A, s_pattern B, s_pattern C, s_prec prec, s_plan* out);
+s_status s_plan_destroy(s_plan plan);
+/* Exact triple count and useful flop count of the plan's product. */
+s_status s_plan_stats(s_plan plan, int64_t* triples, double* flops);
+
+/* C = P_{S_C}(A B): for every block (nu, nu') of S_C,
+ *   C(nu, nu') = sum over lambda with (nu,lambda) in S_A and (lambda,nu') in S_B of
+ *                A(nu,lambda) B(lambda,nu');
+ * no entry outside S_C is formed.  A, B, C are device value buffers on S_A, S_B, S_C in
+ * the plan's element type; C must not alias A or B.  Deterministic: each output entry is
+ * summed by one thread in increasing lambda order. */
+s_status s_mul_masked(s_plan plan, const void* A, const void* B, void* C, void* stream);
+
+/* Adjoint of s_mul_masked (reverse mode):  dA = P_{S_A}(dC B^T),  dB = P_{S_B}(A^T dC).
+ * Either output may be NULL to skip it.  Same element type as the plan. */
+s_status s_mul_masked_adjoint(s_plan plan, const void* dC, const void* A, const void* B, void* dA, void* dB,
+                              void* stream);
+
+/* ---- addition, Sec. 4.1 ---------------------------------------------------------------- */
+
+/* C = alpha A + beta B + gamma I on one pattern (B may be NULL when beta = 0; gamma != 0
+ * needs every non-empty diagonal block in the pattern, else S_ERR_PATTERN).  prec selects
+ * double (S_FP64) or float (S_FP32) buffers.  C may alias A or B. */
+s_status s_add(s_pattern p, s_prec prec, double alpha, const void* A, double beta, const void* B, double gamma,
+               void* C, void* stream);
+
+/* ---- norm estimate and matrix functions ---------------------------------------------- */
+
+/* Largest eigenvalue of a symmetric A (double buffer) by `iters` power steps with
+ * Rayleigh quotients (Sec. 5.3), start vector all ones; the result is written to host
+ * *lambda (the call synchronises the stream). */
+s_status s_norm_est(s_pattern p, const double* A, int iters, double* lambda, void* stream);
+
+typedef struct {
+  int steps;          /* Newton-Schulz steps (S_SQRT); 0 = 25                              */
+  int taylor_degree;  /* Taylor degree (S_EXP, S_EXP_NEG); 0 = 8                            */
+  s_prec prec;        /* arithmetic of the products: S_FP64, S_FP64_DF or S_FP32            */
+  double scale;       /* S_SQRT: c with Y_0 = A/c (0 = 1.01 * norm estimate);
+                         S_EXP*: lambda used for the squaring count (0 = norm estimate)     */
+  int squarings;      /* S_EXP*: -1 = from lambda, else forced count                        */
+  double* residual;   /* optional host out: S_SQRT residual ||P_S(X X) - A||_F / ||A||_F    */
+  void* checkpoints;  /* optional device buffer of 2*steps*nnz doubles: (Y_k, Z_k) per step */
+} s_funm_opts;
+
+/* F = f(A) on A's pattern, every product masked to that pattern (the pattern must hold
+ * its diagonal blocks).  A and F are double device buffers.
+ *   S_SQRT     A^{1/2} by coupled Newton-Schulz: Y_0 = A/c, Z_0 = I,
+ *              T_k = (3I - P_S(Z_k Y_k))/2, Y_{k+1} = P_S(Y_k T_k), Z_{k+1} = P_S(T_k Z_k),
+ *              F = sqrt(c) Y_steps.
+ *   S_EXP, S_EXP_NEG   exp(+-A) by the power series of Sec. 4.4 truncated at the Taylor
+ *              degree, Horner's rule on X = +-A/2^s, then s masked squarings,
+ *              s = max(0, ceil(log2(lambda/0.5))).
+ * Synchronises the stream once (norm estimate) unless opts->scale is given. */
+s_status s_funm(s_pattern p, s_fn fn, const double* A, double* F, const s_funm_opts* opts, void* stream);
+
+/* ---- diagnostics ------------------------------------------------------------------------ */
+const char* s_last_error(void);
+/* Library version string. */
+const char* s_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SFORMAT_H */

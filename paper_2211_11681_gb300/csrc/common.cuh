@@ -1,0 +1,109 @@
+// Internal definitions shared by the translation units of libsformat.so.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "sformat.h"
+
+namespace sf {
+
+// Thread-local error message; set_error returns the status for `return set_error(...)`.
+s_status set_error(s_status st, const std::string& msg);
+s_status cuda_error(cudaError_t e, const char* what);
+
+#define SF_CUDA(call)                                     \
+  do {                                                    \
+    cudaError_t e_ = (call);                              \
+    if (e_ != cudaSuccess) return sf::cuda_error(e_, #call); \
+  } while (0)
+
+// Device copy of a block pattern (Sec. 3.3: cluster pairs of one tree), with the
+// block-CSR rows and the transposed (block-CSC) index, both sorted.
+struct DevPattern {
+  int32_t nc = 0;
+  int64_t n = 0;        // matrix dimension
+  int64_t nblocks = 0;
+  int64_t nnz = 0;
+  int32_t max_bsize = 0;
+  // device arrays
+  int32_t* bsize = nullptr;   // nc
+  int64_t* boff = nullptr;    // nc+1 row offsets
+  int64_t* rowptr = nullptr;  // nc+1
+  int32_t* colidx = nullptr;  // nblocks
+  int32_t* brow = nullptr;    // nblocks: block row of each block
+  int64_t* voff = nullptr;    // nblocks+1 entry offsets
+  int64_t* colptr = nullptr;  // nc+1 (CSC)
+  int32_t* rowidx = nullptr;  // nblocks: block rows of column, sorted
+  int32_t* cscblk = nullptr;  // nblocks: CSR block index of each CSC entry
+  int32_t* diag = nullptr;    // nc: block index of (nu,nu) or -1
+};
+
+}  // namespace sf
+
+struct s_pattern_t {
+  sf::DevPattern d;
+  // host copies
+  std::vector<int32_t> bsize, level, colidx, brow, diag;
+  std::vector<int64_t> boff, rowptr, voff;
+  uint64_t tree_hash = 0;
+  bool has_all_diag = true;
+};
+
+namespace sf {
+
+// One side of a masked product: op(X) with op = identity or transpose.  The index list
+// of row nu of op(X) is idx[ptr[nu] .. ptr[nu+1]) with X block ids blk[...].
+struct Side {
+  const int64_t* ptr;
+  const int32_t* idx;
+  const int32_t* blk;  // nullptr: blk = position (CSR of X itself)
+  const int64_t* voff;
+  bool trans;
+};
+
+// Work item of the product kernels: one output tile of one block of C.
+struct Tile {
+  int32_t blk;  // C block id
+  int16_t r0;   // first row of the tile inside the block
+  int16_t c0;   // first column
+};
+
+struct MulDesc {
+  Side x, y;                 // C = op(X) op(Y) on S_C
+  const s_pattern_t* pc;
+  const s_pattern_t* px;
+  const s_pattern_t* py;
+  Tile* tiles = nullptr;     // device tile list, heaviest first
+  int64_t ntiles = 0;
+  unsigned int* counter = nullptr;  // device work counter
+  int64_t triples = 0;
+  double flops = 0.0;
+};
+
+s_status build_desc(const s_pattern_t* X, bool tx, const s_pattern_t* Y, bool ty, const s_pattern_t* C, s_prec prec,
+                    MulDesc* d);
+void free_desc(MulDesc* d);
+s_status run_mul(const MulDesc& d, s_prec prec, const void* X, const void* Y, void* C, cudaStream_t st);
+
+// Element-wise kernels (add.cu)
+s_status run_add(const s_pattern_t* p, s_prec prec, double alpha, const void* A, double beta, const void* B,
+                 double gamma, void* C, cudaStream_t st);
+s_status run_spmv_f64(const s_pattern_t* p, const double* A, const double* x, double* y, cudaStream_t st);
+
+constexpr int kTile = 20;  // output tile edge of the product kernels
+
+}  // namespace sf
+
+struct s_plan_t {
+  s_prec prec;
+  const s_pattern_t* a;
+  const s_pattern_t* b;
+  const s_pattern_t* c;
+  sf::MulDesc fwd;
+  sf::MulDesc adjA;  // dA = P_{S_A}(dC B^T), built on first use
+  sf::MulDesc adjB;  // dB = P_{S_B}(A^T dC)
+  bool adj_built = false;
+};

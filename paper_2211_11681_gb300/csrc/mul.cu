@@ -1,0 +1,455 @@
+// Masked block-sparse product C = P_{S_C}(op(X) op(Y)), Eq. (product) of Thm. (product),
+// Sec. 4.1, and its symbolic phase.
+//
+// Work decomposition: every block (nu, nu') of S_C is cut into output tiles of at most
+// kTile x kTile entries; one warp owns one tile for the whole lambda-sum, so each output
+// entry is accumulated by one thread in increasing lambda order (deterministic, no
+// atomics).  The lambda set of a tile is the intersection of the sorted block-index lists
+// row(op(X), nu) and col(op(Y), nu'); a warp intersects them 32 entries of the X list at a
+// time by binary search in the Y list.  Warps take tiles from a device counter
+// (persistent grid sized to the SM count); tiles are ordered heaviest first.
+#include <cub/cub.cuh>
+
+#include <algorithm>
+#include <cstring>
+#include <new>
+
+#include "common.cuh"
+
+namespace sf {
+
+struct DevSide {
+  const int64_t* ptr;
+  const int32_t* idx;
+  const int32_t* blk;
+  const int64_t* voff;
+};
+
+struct MulArgs {
+  DevSide x, y;
+  const int32_t* bsize;
+  const int32_t* c_brow;
+  const int32_t* c_col;
+  const int64_t* c_voff;
+  const Tile* tiles;
+  int64_t ntiles;
+  unsigned int* counter;
+};
+
+static DevSide dev_side(const Side& s) { return DevSide{s.ptr, s.idx, s.blk, s.voff}; }
+
+__device__ __forceinline__ int lower_bound_dev(const int32_t* a, int lo, int hi, int32_t v) {
+  while (lo < hi) {
+    int mid = (lo + hi) >> 1;
+    if (__ldg(a + mid) < v) lo = mid + 1;
+    else hi = mid;
+  }
+  return lo;
+}
+
+// ---- symbolic: per C block, matched lambda count and useful flops ----------------------
+__global__ void count_kernel(DevSide x, DevSide y, const int32_t* bsize, const int32_t* c_brow, const int32_t* c_col,
+                             int64_t nblocks, unsigned long long* triples, double* block_flops) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t k = warp; k < nblocks; k += nwarps) {
+    const int nu = c_brow[k], nup = c_col[k];
+    const int px0 = (int)x.ptr[nu], px1 = (int)x.ptr[nu + 1];
+    int py0 = (int)y.ptr[nup];
+    const int py1 = (int)y.ptr[nup + 1];
+    double fl = 0.0;
+    unsigned int cnt = 0;
+    for (int base = px0; base < px1 && py0 < py1; base += 32) {
+      const int i = base + lane;
+      const int32_t lam = i < px1 ? __ldg(x.idx + i) : INT32_MAX;
+      const int pos = lower_bound_dev(y.idx, py0, py1, lam);
+      const bool hit = i < px1 && pos < py1 && __ldg(y.idx + pos) == lam;
+      if (hit) {
+        cnt++;
+        fl += 2.0 * bsize[lam];
+      }
+      const int last = __shfl_sync(0xffffffffu, pos, 31);
+      py0 = last;
+    }
+    for (int o = 16; o; o >>= 1) {
+      cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
+      fl += __shfl_xor_sync(0xffffffffu, fl, o);
+    }
+    if (lane == 0) {
+      block_flops[k] = fl * bsize[nu] * bsize[nup];
+      atomicAdd(triples, (unsigned long long)cnt);
+    }
+  }
+}
+
+// tiles per block
+__global__ void tile_count_kernel(const int32_t* bsize, const int32_t* c_brow, const int32_t* c_col, int64_t nblocks,
+                                  int32_t* ntile) {
+  int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (k >= nblocks) return;
+  int ni = bsize[c_brow[k]], nj = bsize[c_col[k]];
+  ntile[k] = ((ni + kTile - 1) / kTile) * ((nj + kTile - 1) / kTile);
+}
+
+__global__ void tile_fill_kernel(const int32_t* order, const int64_t* first, const int32_t* bsize,
+                                 const int32_t* c_brow, const int32_t* c_col, int64_t nblocks, Tile* tiles) {
+  int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (s >= nblocks) return;
+  int k = order[s];
+  int ni = bsize[c_brow[k]], nj = bsize[c_col[k]];
+  int64_t t = first[s];
+  for (int r0 = 0; r0 < ni; r0 += kTile)
+    for (int c0 = 0; c0 < nj; c0 += kTile) tiles[t++] = Tile{k, (int16_t)r0, (int16_t)c0};
+}
+
+// ---- numeric kernels ----------------------------------------------------------------------
+constexpr int kWarps = 8;
+template <typename T>
+constexpr bool kCompensated = sizeof(T) == 4;
+constexpr int kPer = (kTile * kTile + 31) / 32;  // accumulators per lane
+
+template <typename T, bool TX, bool TY>
+__global__ void __launch_bounds__(kWarps * 32) mul_kernel(MulArgs a, const T* __restrict__ X,
+                                                          const T* __restrict__ Y, T* __restrict__ C) {
+  __shared__ T sX[kWarps][kTile * kTile];
+  __shared__ T sY[kWarps][kTile * kTile];
+  const int lane = threadIdx.x & 31;
+  const int w = threadIdx.x >> 5;
+  T* xs = sX[w];
+  T* ys = sY[w];
+  for (;;) {
+    unsigned int t = 0;
+    if (lane == 0) t = atomicAdd(a.counter, 1u);
+    t = __shfl_sync(0xffffffffu, t, 0);
+    if (t >= a.ntiles) break;
+    const Tile tile = a.tiles[t];
+    const int k = tile.blk;
+    const int nu = a.c_brow[k], nup = a.c_col[k];
+    const int ni = a.bsize[nu], nj = a.bsize[nup];
+    const int th = min(kTile, ni - tile.r0), tw = min(kTile, nj - tile.c0);
+    const int nout = th * tw;
+    T acc[kPer], comp[kPer];
+#pragma unroll
+    for (int m = 0; m < kPer; ++m) acc[m] = comp[m] = T(0);
+    const int px0 = (int)a.x.ptr[nu], px1 = (int)a.x.ptr[nu + 1];
+    int py0 = (int)a.y.ptr[nup];
+    const int py1 = (int)a.y.ptr[nup + 1];
+    for (int base = px0; base < px1 && py0 < py1; base += 32) {
+      const int i = base + lane;
+      const int32_t lam = i < px1 ? __ldg(a.x.idx + i) : INT32_MAX;
+      const int pos = lower_bound_dev(a.y.idx, py0, py1, lam);
+      const bool hit = i < px1 && pos < py1 && __ldg(a.y.idx + pos) == lam;
+      unsigned int mask = __ballot_sync(0xffffffffu, hit);
+      const int kx = hit ? (a.x.blk ? __ldg(a.x.blk + i) : i) : 0;
+      const int ky = hit ? (a.y.blk ? __ldg(a.y.blk + pos) : pos) : 0;
+      py0 = __shfl_sync(0xffffffffu, pos, 31);
+      while (mask) {
+        const int l = __ffs(mask) - 1;
+        mask &= mask - 1;
+        const int lm = __shfl_sync(0xffffffffu, lam, l);
+        const int bx = __shfl_sync(0xffffffffu, kx, l);
+        const int by = __shfl_sync(0xffffffffu, ky, l);
+        const int nl = a.bsize[lm];
+        const T* xb = X + a.x.voff[bx];
+        const T* yb = Y + a.y.voff[by];
+        for (int t0 = 0; t0 < nl; t0 += kTile) {
+          const int tk = min(kTile, nl - t0);
+          // op(X)(r0+r, t0+t) -> xs[r*tk+t];  op(Y)(t0+t, c0+c) -> ys[t*tw+c]
+          for (int e = lane; e < th * tk; e += 32) {
+            const int r = e / tk, tt = e - r * tk;
+            const int gr = tile.r0 + r, gt = t0 + tt;
+            xs[e] = TX ? xb[(int64_t)gt * ni + gr] : xb[(int64_t)gr * nl + gt];
+          }
+          for (int e = lane; e < tk * tw; e += 32) {
+            const int tt = e / tw, c = e - tt * tw;
+            const int gt = t0 + tt, gc = tile.c0 + c;
+            ys[e] = TY ? yb[(int64_t)gc * nl + gt] : yb[(int64_t)gt * nj + gc];
+          }
+          __syncwarp();
+#pragma unroll
+          for (int m = 0; m < kPer; ++m) {
+            const int e = lane + 32 * m;
+            if (e < nout) {
+              const int r = e / tw, c = e - r * tw;
+              const T* xr = xs + r * tk;
+              const T* yc = ys + c;
+              if (kCompensated<T>) {
+                // float: partial over this lambda block, then an error-free two-sum into
+                // (acc, comp); the long lambda-sums would otherwise lose ~1e-6 (Sec. 4.1
+                // sums over all lambda levels)
+                T s = T(0);
+                for (int tt = 0; tt < tk; ++tt) s = fma(xr[tt], yc[tt * tw], s);
+                const T hi = acc[m] + s;
+                const T bp = hi - acc[m];
+                comp[m] += (acc[m] - (hi - bp)) + (s - bp);
+                acc[m] = hi;
+              } else {
+                T s = acc[m];
+                for (int tt = 0; tt < tk; ++tt) s = fma(xr[tt], yc[tt * tw], s);
+                acc[m] = s;
+              }
+            }
+          }
+          __syncwarp();
+        }
+      }
+    }
+    T* cb = C + a.c_voff[k];
+#pragma unroll
+    for (int m = 0; m < kPer; ++m) {
+      const int e = lane + 32 * m;
+      if (e < nout) {
+        const int r = e / tw, c = e - r * tw;
+        cb[(int64_t)(tile.r0 + r) * nj + tile.c0 + c] = kCompensated<T> ? acc[m] + comp[m] : acc[m];
+      }
+    }
+  }
+}
+
+static int g_sms = 0;
+static int num_sms() {
+  if (!g_sms) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&g_sms, cudaDevAttrMultiProcessorCount, dev);
+    if (g_sms <= 0) g_sms = 1;
+  }
+  return g_sms;
+}
+
+static Side side_of(const s_pattern_t* p, bool row_side, bool trans) {
+  // row_side: the list indexed by the output row (X side); otherwise by the output column.
+  const DevPattern& d = p->d;
+  bool use_csr = row_side ? !trans : trans;
+  if (use_csr) return Side{d.rowptr, d.colidx, nullptr, d.voff, trans};
+  return Side{d.colptr, d.rowidx, d.cscblk, d.voff, trans};
+}
+
+s_status build_desc(const s_pattern_t* X, bool tx, const s_pattern_t* Y, bool ty, const s_pattern_t* C, s_prec prec,
+                    MulDesc* out) {
+  (void)prec;
+  MulDesc d;
+  d.x = side_of(X, true, tx);
+  d.y = side_of(Y, false, ty);
+  d.pc = C;
+  d.px = X;
+  d.py = Y;
+  const int64_t nb = C->d.nblocks;
+  unsigned long long* dtrip = nullptr;
+  double* bflops = nullptr;
+  int32_t* ntile = nullptr;
+  int32_t* order_in = nullptr;
+  int32_t* order = nullptr;
+  double* keys_out = nullptr;
+  int64_t* first = nullptr;
+  void* tmp = nullptr;
+  size_t tmp_bytes = 0, need = 0;
+  s_status st = S_OK;
+  cudaError_t e;
+#define TRY(call)                         \
+  do {                                    \
+    e = (call);                           \
+    if (e != cudaSuccess) {               \
+      st = cuda_error(e, #call);          \
+      goto done;                          \
+    }                                     \
+  } while (0)
+  TRY(cudaMalloc(&dtrip, sizeof(unsigned long long)));
+  TRY(cudaMemset(dtrip, 0, sizeof(unsigned long long)));
+  TRY(cudaMalloc(&bflops, sizeof(double) * std::max<int64_t>(nb, 1)));
+  TRY(cudaMalloc(&ntile, sizeof(int32_t) * std::max<int64_t>(nb, 1)));
+  TRY(cudaMalloc(&order_in, sizeof(int32_t) * std::max<int64_t>(nb, 1)));
+  TRY(cudaMalloc(&order, sizeof(int32_t) * std::max<int64_t>(nb, 1)));
+  TRY(cudaMalloc(&keys_out, sizeof(double) * std::max<int64_t>(nb, 1)));
+  TRY(cudaMalloc(&first, sizeof(int64_t) * (nb + 1)));
+  TRY(cudaMalloc(&d.counter, sizeof(unsigned int)));
+  if (nb > 0) {
+    int threads = 256;
+    int blocks = (int)std::min<int64_t>((nb * 32 + threads - 1) / threads, (int64_t)num_sms() * 16);
+    count_kernel<<<blocks, threads>>>(dev_side(d.x), dev_side(d.y), C->d.bsize, C->d.brow, C->d.colidx, nb, dtrip,
+                                      bflops);
+    TRY(cudaGetLastError());
+    int g = (int)((nb + 255) / 256);
+    tile_count_kernel<<<g, 256>>>(C->d.bsize, C->d.brow, C->d.colidx, nb, ntile);
+    TRY(cudaGetLastError());
+    // order blocks by useful flops, heaviest first
+    {
+      std::vector<int32_t> iota(nb);
+      for (int64_t k = 0; k < nb; ++k) iota[k] = (int32_t)k;
+      TRY(cudaMemcpy(order_in, iota.data(), sizeof(int32_t) * nb, cudaMemcpyHostToDevice));
+    }
+    TRY(cub::DeviceRadixSort::SortPairsDescending(nullptr, need, bflops, keys_out, order_in, order, (int)nb));
+    tmp_bytes = need;
+    TRY(cudaMalloc(&tmp, std::max<size_t>(tmp_bytes, 1)));
+    TRY(cub::DeviceRadixSort::SortPairsDescending(tmp, tmp_bytes, bflops, keys_out, order_in, order, (int)nb));
+    // tiles per block in sorted order, exclusive scan -> first tile of each sorted block
+    {
+      std::vector<int32_t> nt(nb), ord(nb);
+      TRY(cudaMemcpy(nt.data(), ntile, sizeof(int32_t) * nb, cudaMemcpyDeviceToHost));
+      TRY(cudaMemcpy(ord.data(), order, sizeof(int32_t) * nb, cudaMemcpyDeviceToHost));
+      std::vector<int64_t> fst(nb + 1);
+      fst[0] = 0;
+      for (int64_t s = 0; s < nb; ++s) fst[s + 1] = fst[s] + nt[ord[s]];
+      d.ntiles = fst[nb];
+      TRY(cudaMemcpy(first, fst.data(), sizeof(int64_t) * (nb + 1), cudaMemcpyHostToDevice));
+    }
+    TRY(cudaMalloc(&d.tiles, sizeof(Tile) * std::max<int64_t>(d.ntiles, 1)));
+    tile_fill_kernel<<<g, 256>>>(order, first, C->d.bsize, C->d.brow, C->d.colidx, nb, d.tiles);
+    TRY(cudaGetLastError());
+    {
+      unsigned long long tr = 0;
+      TRY(cudaMemcpy(&tr, dtrip, sizeof(tr), cudaMemcpyDeviceToHost));
+      d.triples = (int64_t)tr;
+      std::vector<double> bf(nb);
+      TRY(cudaMemcpy(bf.data(), bflops, sizeof(double) * nb, cudaMemcpyDeviceToHost));
+      double f = 0.0;
+      for (double v : bf) f += v;
+      d.flops = f;
+    }
+  } else {
+    TRY(cudaMalloc(&d.tiles, sizeof(Tile)));
+  }
+done:
+#undef TRY
+  cudaFree(dtrip);
+  cudaFree(bflops);
+  cudaFree(ntile);
+  cudaFree(order_in);
+  cudaFree(order);
+  cudaFree(keys_out);
+  cudaFree(first);
+  cudaFree(tmp);
+  if (st != S_OK) {
+    free_desc(&d);
+    return st;
+  }
+  *out = d;
+  return S_OK;
+}
+
+void free_desc(MulDesc* d) {
+  cudaFree(d->tiles);
+  cudaFree(d->counter);
+  d->tiles = nullptr;
+  d->counter = nullptr;
+  d->ntiles = 0;
+}
+
+template <typename T>
+static s_status launch_typed(const MulDesc& d, const void* X, const void* Y, void* C, cudaStream_t st) {
+  MulArgs a;
+  a.x = dev_side(d.x);
+  a.y = dev_side(d.y);
+  a.bsize = d.pc->d.bsize;
+  a.c_brow = d.pc->d.brow;
+  a.c_col = d.pc->d.colidx;
+  a.c_voff = d.pc->d.voff;
+  a.tiles = d.tiles;
+  a.ntiles = d.ntiles;
+  a.counter = d.counter;
+  if (d.ntiles == 0) return S_OK;
+  SF_CUDA(cudaMemsetAsync(d.counter, 0, sizeof(unsigned int), st));
+  int per_sm = 0;
+  auto kern = d.x.trans ? (d.y.trans ? mul_kernel<T, true, true> : mul_kernel<T, true, false>)
+                        : (d.y.trans ? mul_kernel<T, false, true> : mul_kernel<T, false, false>);
+  SF_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kWarps * 32, 0));
+  if (per_sm < 1) per_sm = 1;
+  int64_t want = (d.ntiles + kWarps - 1) / kWarps;
+  int grid = (int)std::min<int64_t>(want, (int64_t)num_sms() * per_sm);
+  kern<<<grid, kWarps * 32, 0, st>>>(a, (const T*)X, (const T*)Y, (T*)C);
+  SF_CUDA(cudaGetLastError());
+  return S_OK;
+}
+
+s_status run_mul(const MulDesc& d, s_prec prec, const void* X, const void* Y, void* C, cudaStream_t st) {
+  switch (prec) {
+    case S_FP64:
+      return launch_typed<double>(d, X, Y, C, st);
+    case S_FP32:
+      return launch_typed<float>(d, X, Y, C, st);
+    default:
+      return set_error(S_ERR_ARG, "precision not supported by this product path");
+  }
+}
+
+static s_status check_same_tree(const s_pattern_t* a, const s_pattern_t* b) {
+  if (a->tree_hash != b->tree_hash || a->d.nc != b->d.nc)
+    return set_error(S_ERR_MISMATCH, "operands come from different cluster trees");
+  return S_OK;
+}
+
+}  // namespace sf
+
+using namespace sf;
+
+extern "C" s_status s_plan_create(s_pattern A, s_pattern B, s_pattern C, s_prec prec, s_plan* out) {
+  if (!out) return set_error(S_ERR_ARG, "s_plan_create: out is NULL");
+  *out = nullptr;
+  if (!A || !B || !C) return set_error(S_ERR_ARG, "s_plan_create: NULL pattern");
+  if (prec != S_FP64 && prec != S_FP32) return set_error(S_ERR_ARG, "s_plan_create: unsupported precision");
+  s_status st;
+  if ((st = check_same_tree(A, B)) || (st = check_same_tree(A, C))) return st;
+  s_plan_t* p = new (std::nothrow) s_plan_t();
+  if (!p) return set_error(S_ERR_NOMEM, "host allocation");
+  p->prec = prec;
+  p->a = A;
+  p->b = B;
+  p->c = C;
+  if ((st = build_desc(A, false, B, false, C, prec, &p->fwd))) {
+    delete p;
+    return st;
+  }
+  *out = p;
+  return S_OK;
+}
+
+extern "C" s_status s_plan_destroy(s_plan p) {
+  if (!p) return S_OK;
+  free_desc(&p->fwd);
+  if (p->adj_built) {
+    free_desc(&p->adjA);
+    free_desc(&p->adjB);
+  }
+  delete p;
+  return S_OK;
+}
+
+extern "C" s_status s_plan_stats(s_plan p, int64_t* triples, double* flops) {
+  if (!p) return set_error(S_ERR_ARG, "s_plan_stats: NULL plan");
+  if (triples) *triples = p->fwd.triples;
+  if (flops) *flops = p->fwd.flops;
+  return S_OK;
+}
+
+extern "C" s_status s_mul_masked(s_plan p, const void* A, const void* B, void* C, void* stream) {
+  if (!p || !A || !B || !C) return set_error(S_ERR_ARG, "s_mul_masked: NULL argument");
+  if (C == A || C == B) return set_error(S_ERR_ARG, "s_mul_masked: C aliases an input");
+  return run_mul(p->fwd, p->prec, A, B, C, (cudaStream_t)stream);
+}
+
+extern "C" s_status s_mul_masked_adjoint(s_plan p, const void* dC, const void* A, const void* B, void* dA, void* dB,
+                                         void* stream) {
+  if (!p || !dC) return set_error(S_ERR_ARG, "s_mul_masked_adjoint: NULL argument");
+  if (!p->adj_built) {
+    s_status st;
+    // dA = P_{S_A}(dC B^T): X = dC on S_C (as is), Y = B transposed, output S_A
+    if ((st = build_desc(p->c, false, p->b, true, p->a, p->prec, &p->adjA))) return st;
+    // dB = P_{S_B}(A^T dC): X = A transposed, Y = dC as is, output S_B
+    if ((st = build_desc(p->a, true, p->c, false, p->b, p->prec, &p->adjB))) {
+      free_desc(&p->adjA);
+      return st;
+    }
+    p->adj_built = true;
+  }
+  s_status st = S_OK;
+  if (dA) {
+    if (!B) return set_error(S_ERR_ARG, "s_mul_masked_adjoint: dA needs B");
+    if ((st = run_mul(p->adjA, p->prec, dC, B, dA, (cudaStream_t)stream))) return st;
+  }
+  if (dB) {
+    if (!A) return set_error(S_ERR_ARG, "s_mul_masked_adjoint: dB needs A");
+    if ((st = run_mul(p->adjB, p->prec, A, dC, dB, (cudaStream_t)stream))) return st;
+  }
+  return S_OK;
+}

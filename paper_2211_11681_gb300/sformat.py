@@ -1,0 +1,196 @@
+"""Python binding of libsformat.so (C ABI in include/sformat.h): argument marshalling only.
+
+Value buffers are torch CUDA tensors (float64 or float32, contiguous); patterns are built
+from numpy arrays.  Every call checks the returned status and raises ``SFormatError``
+carrying the library's message.  There is no fallback: if the shared library is missing
+the import of this module fails.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_lib", "libsformat.so")
+
+S_OK, S_ERR_ARG, S_ERR_PATTERN, S_ERR_MISMATCH, S_ERR_NOMEM, S_ERR_CUDA, S_ERR_NOT_CONVERGED, S_ERR_TIMEOUT = \
+    0, -1, -2, -3, -4, -5, -6, -7
+S_FP64, S_FP32, S_BF16X3, S_FP64_DF = 0, 1, 2, 3
+S_SQRT, S_EXP, S_EXP_NEG = 0, 1, 2
+
+PREC = {"fp64": S_FP64, "fp32": S_FP32, "bf16x3": S_BF16X3, "fp64_df": S_FP64_DF}
+
+
+class SFormatError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("sformat status %d: %s" % (status, msg))
+        self.status = status
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError("libsformat.so is not built (%s); run paper_2211_11681_gb300.build.build()" % LIB_PATH)
+    lib = ctypes.CDLL(LIB_PATH)
+    i32, i64, vp, dbl = ctypes.c_int32, ctypes.c_int64, ctypes.c_void_p, ctypes.c_double
+    P = ctypes.POINTER
+    sig = {
+        "s_pattern_create": (i32, [i32, P(i64), P(i32), P(i64), P(i32), P(vp)]),
+        "s_pattern_destroy": (i32, [vp]),
+        "s_pattern_nnz": (i64, [vp]),
+        "s_pattern_nblocks": (i64, [vp]),
+        "s_pattern_block_offsets": (i32, [vp, P(i64)]),
+        "s_plan_create": (i32, [vp, vp, vp, i32, P(vp)]),
+        "s_plan_destroy": (i32, [vp]),
+        "s_plan_stats": (i32, [vp, P(i64), P(dbl)]),
+        "s_mul_masked": (i32, [vp, vp, vp, vp, vp]),
+        "s_mul_masked_adjoint": (i32, [vp, vp, vp, vp, vp, vp, vp]),
+        "s_add": (i32, [vp, i32, dbl, vp, dbl, vp, dbl, vp, vp]),
+        "s_norm_est": (i32, [vp, vp, i32, P(dbl), vp]),
+        "s_funm": (i32, [vp, i32, vp, vp, vp, vp]),
+        "s_last_error": (ctypes.c_char_p, []),
+        "s_version": (ctypes.c_char_p, []),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    return lib
+
+
+lib = _load()
+
+
+class FunmOpts(ctypes.Structure):
+    _fields_ = [("steps", ctypes.c_int), ("taylor_degree", ctypes.c_int), ("prec", ctypes.c_int),
+                ("scale", ctypes.c_double), ("squarings", ctypes.c_int),
+                ("residual", ctypes.POINTER(ctypes.c_double)), ("checkpoints", ctypes.c_void_p)]
+
+
+def check(st):
+    if st != S_OK:
+        raise SFormatError(st, lib.s_last_error().decode())
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    if not t.is_contiguous():
+        raise ValueError("value buffers must be contiguous")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _a(x, dt):
+    return np.ascontiguousarray(x, dtype=dt)
+
+
+class Pattern:
+    """A block pattern S on the device (s_pattern_create)."""
+
+    def __init__(self, block_offset, level, rowptr, colidx):
+        self._bo = _a(block_offset, np.int64)
+        self._lv = _a(level, np.int32)
+        self._rp = _a(rowptr, np.int64)
+        self._ci = _a(colidx, np.int32)
+        h = ctypes.c_void_p()
+        P = ctypes.POINTER
+        check(lib.s_pattern_create(len(self._bo) - 1, self._bo.ctypes.data_as(P(ctypes.c_int64)),
+                                   self._lv.ctypes.data_as(P(ctypes.c_int32)),
+                                   self._rp.ctypes.data_as(P(ctypes.c_int64)),
+                                   self._ci.ctypes.data_as(P(ctypes.c_int32)), ctypes.byref(h)))
+        self.h = h
+
+    @property
+    def nnz(self):
+        return int(lib.s_pattern_nnz(self.h))
+
+    @property
+    def nblocks(self):
+        return int(lib.s_pattern_nblocks(self.h))
+
+    def block_offsets(self):
+        out = np.zeros(self.nblocks + 1, dtype=np.int64)
+        check(lib.s_pattern_block_offsets(self.h, out.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))))
+        return out
+
+    def close(self):
+        if getattr(self, "h", None) is not None and self.h.value:
+            lib.s_pattern_destroy(self.h)
+            self.h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Plan:
+    """Symbolic phase of C = P_{S_C}(A B) (s_plan_create)."""
+
+    def __init__(self, A, B, C, prec="fp64"):
+        self.prec = PREC[prec] if isinstance(prec, str) else int(prec)
+        self.pats = (A, B, C)           # the patterns must outlive the plan
+        h = ctypes.c_void_p()
+        check(lib.s_plan_create(A.h, B.h, C.h, self.prec, ctypes.byref(h)))
+        self.h = h
+
+    def stats(self):
+        t = ctypes.c_int64()
+        f = ctypes.c_double()
+        check(lib.s_plan_stats(self.h, ctypes.byref(t), ctypes.byref(f)))
+        return int(t.value), float(f.value)
+
+    def mul(self, A, B, C, stream=None):
+        check(lib.s_mul_masked(self.h, _ptr(A), _ptr(B), _ptr(C), _stream(stream)))
+        return C
+
+    def adjoint(self, dC, A, B, dA=None, dB=None, stream=None):
+        check(lib.s_mul_masked_adjoint(self.h, _ptr(dC), _ptr(A), _ptr(B), _ptr(dA), _ptr(dB), _stream(stream)))
+        return dA, dB
+
+    def close(self):
+        if getattr(self, "h", None) is not None and self.h.value:
+            lib.s_plan_destroy(self.h)
+            self.h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def add(pattern, A, B, C, alpha=1.0, beta=1.0, gamma=0.0, prec="fp64", stream=None):
+    p = PREC[prec] if isinstance(prec, str) else int(prec)
+    check(lib.s_add(pattern.h, p, float(alpha), _ptr(A), float(beta), _ptr(B), float(gamma), _ptr(C),
+                    _stream(stream)))
+    return C
+
+
+def norm_est(pattern, A, iters=50, stream=None):
+    lam = ctypes.c_double()
+    check(lib.s_norm_est(pattern.h, _ptr(A), int(iters), ctypes.byref(lam), _stream(stream)))
+    return float(lam.value)
+
+
+def funm(pattern, fn, A, F, steps=0, taylor_degree=0, prec="fp64", scale=0.0, squarings=-1, residual=False,
+         checkpoints=None, stream=None):
+    """F = f(A) with f in {"sqrt", "exp", "exp_neg"}; returns the residual for sqrt if asked."""
+    code = {"sqrt": S_SQRT, "exp": S_EXP, "exp_neg": S_EXP_NEG}[fn]
+    res = ctypes.c_double(-1.0)
+    o = FunmOpts(int(steps), int(taylor_degree), PREC[prec] if isinstance(prec, str) else int(prec),
+                 float(scale), int(squarings), ctypes.pointer(res) if residual else None,
+                 _ptr(checkpoints))
+    check(lib.s_funm(pattern.h, code, _ptr(A), _ptr(F), ctypes.byref(o), _stream(stream)))
+    return float(res.value) if residual else None
+
+
+def version():
+    return lib.s_version().decode()

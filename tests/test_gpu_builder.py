@@ -1,0 +1,53 @@
+"""The product-side input builder (C++ tree/basis/pattern, device values) against the
+oracle's builder: identical trees, block sizes and eta patterns (integer work: bit-exact),
+samplet transforms equal to rounding, and device values P_S(T K T^T) equal to the
+oracle's within float rounding (the device evaluates the kernel and the transforms in
+float: relative error ~1e-6 of the largest entry)."""
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle.pipeline import compress_kernel
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.mark.parametrize("wname,n", [("matern32_2d_4096", 2048), ("matern12_3d_1m", 3000),
+                                     ("matern52_sphere", 1500)])
+def test_builder_matches_oracle(wname, n):
+    from paper_2211_11681_gb300.builder import Builder
+    from tests.gpu_util import host
+    w = W.WORKLOADS[wname]
+    x = W.points(w, n)
+    c = compress_kernel(x, w.nu, w.ell, w.q, w.leaf, w.eta, 0.0, 1.0 / n, w.nugget)
+    b = Builder(x, w.leaf, w.q, w.eta)
+    np.testing.assert_array_equal(b.block_offset, c.A.boff)
+    np.testing.assert_array_equal(b.rowptr, c.rowptr_eta)
+    np.testing.assert_array_equal(b.colidx, c.colidx_eta)
+    np.testing.assert_array_equal(b.perm, c.clusters[0].idx)
+    if w.domain != "sphere":       # the sphere's moment matrices are rank deficient: the
+        T = b.dense_transform()    # samplet completion is not unique
+        np.testing.assert_allclose(T, c.basis.T, atol=1e-12)
+        pat, vals = b.values(w.nu, w.ell, 1.0 / n, w.nugget, 0.0)
+        assert pat.nblocks == c.A.nblocks
+        np.testing.assert_array_equal(pat.block_offsets(), c.A.voff)
+        got = host(vals)
+        ref = c.A.val
+        assert np.abs(got - ref).max() <= 2e-6 * np.abs(ref).max()
+    else:
+        T = b.dense_transform()
+        np.testing.assert_allclose(T @ T.T, np.eye(n), atol=1e-13)
+
+
+def test_builder_threshold_is_symmetric_and_close_to_oracle():
+    from paper_2211_11681_gb300.builder import Builder
+    w = W.WORKLOADS["matern12_3d_1m"]
+    n = 4096
+    x = W.points(w, n)
+    c = compress_kernel(x, w.nu, w.ell, w.q, w.leaf, w.eta, w.tau, 1.0 / n, w.nugget)
+    b = Builder(x, w.leaf, w.q, w.eta)
+    pat, vals = b.values(w.nu, w.ell, 1.0 / n, w.nugget, w.tau)
+    off = pat.block_offsets()
+    assert off[-1] == pat.nnz
+    # kept blocks agree with the oracle's FP64 decision up to a few borderline blocks
+    assert abs(pat.nblocks - c.A.nblocks) <= max(3, c.A.nblocks // 1000)
