@@ -1,0 +1,352 @@
+#!/usr/bin/env python3
+"""Benchmark of the masked S-format product C = P_S(A A) (Eq. (product), Sec. 4.1).
+
+Workload (default ``matern12_3d_1m``): N = 2^20 points uniform in [0,1]^3, Matern-1/2
+kernel with lengthscale 0.1 scaled by 1/N, samplets with vanishing moments up to degree 3
+(20 moments), leaf size 32, eta = 1.0, a-posteriori threshold 1e-8; C on A's own pattern.
+Inputs are prepared before timing (cluster tree and pattern on the host, values on the
+device) and stay resident in HBM.
+
+One step = one masked product in the mixed arithmetic (float inputs, float products,
+compensated float accumulation).  ``value`` is useful GFLOP/s (exact flop count of the
+symbolic phase, no padding).  The same product in FP64 is run once for the comparison
+and the relative Frobenius error of the mixed result against it is reported.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+``--impl reference`` times the plain-C FP64 oracle on the host cores on a bounded sample
+of output blocks of the same workload.  Under torchrun every rank runs its own replica
+(the product does not shard across GPUs here) and rank 0 prints one JSON line.
+"""
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "masked S-product GFLOP/s & HBM GB/s, N=2^20 d=3; mixed vs FP64 at 1e-6 rel err"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", default="matern12_3d_1m")
+    ap.add_argument("--n", type=int, default=0, help="override N (smaller runs for checks)")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0, help="target CPU time of the oracle sample")
+    ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------------------------------
+def workload_config(w, n, pat, triples, flops):
+    nnz = pat.nnz
+    return {
+        "workload": w.name, "n": n, "d": w.d, "domain": w.domain, "kernel": "matern-%g" % w.nu, "ell": w.ell,
+        "kernel_scale": "1/N", "nugget": w.nugget, "q": w.q, "leaf": w.leaf, "eta": w.eta, "tau": w.tau,
+        "blocks": pat.nblocks, "nnz": nnz, "triples": triples, "flops_per_product": flops,
+        "l2": "inputs larger than L2 (A is %.2f GB in float), no flush" % (nnz * 4 / 1e9),
+        "product": "C = P_S(A A) on A's pattern",
+    }
+
+
+def build_input(w, n):
+    import workloads as W
+    from paper_2211_11681_gb300.builder import Builder
+    x = W.points(w, n)
+    t0 = time.time()
+    b = Builder(x, w.leaf, w.q, w.eta)
+    t1 = time.time()
+    pat, vals = b.values(w.nu, w.ell, 1.0 / n, w.nugget, w.tau)
+    t2 = time.time()
+    return b, pat, vals, {"host_s": round(t1 - t0, 2), "values_s": round(t2 - t1, 2)}
+
+
+def algorithmic_bytes(pat, width):
+    # each operand read once, C written once, plus the pattern's index arrays
+    bo, rp, ci = pat.arrays()
+    idx = 8 * (len(bo) + len(rp)) + 4 * len(ci)
+    return width * 3 * pat.nnz + 3 * idx
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+    FIELDS = ("uuid,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, uuid):
+        self.uuid = uuid
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
+                                          "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.th = threading.Thread(target=self._read, daemon=True)
+            self.th.start()
+        except (OSError, ValueError):
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            time.sleep(0.25)
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        rows = []
+        for ln in self.lines:
+            f = [s.strip() for s in ln.split(",")]
+            if len(f) < 9:
+                continue
+            if self.uuid and f[0] != self.uuid and any(r[0] == self.uuid for r in rows):
+                continue
+            rows.append(f)
+        mine = [r for r in rows if r[0] == self.uuid] or rows
+        if not mine:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        sm = [float(r[1]) for r in mine if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in mine if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in mine for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(mine)}
+
+
+def kernel_traffic():
+    """Per-launch DRAM bytes of the product kernel from the committed ncu summary, if it
+    was taken on the current kernel source; else None."""
+    path = os.path.join(ROOT, "profiles", "mul_f32_traffic.json")
+    src = os.path.join(ROOT, "paper_2211_11681_gb300", "csrc", "mul.cu")
+    try:
+        with open(path) as f:
+            rec = json.load(f)
+        sha = hashlib.sha256(open(src, "rb").read()).hexdigest()
+        if rec.get("source_sha256") != sha:
+            return None
+        return rec.get("dram_bytes_per_launch")
+    except (OSError, ValueError):
+        return None
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except (OSError, ValueError):
+        return {}
+
+
+# ---------------------------------------------------------------------------------------
+def oracle_sample(pat, vals_host, cpu_seconds, seed=0):
+    """Time the plain-C FP64 oracle on a bounded random sample of output blocks, using all
+    host cores.  Returns (GFLOP/s, cores, description, seconds)."""
+    from oracle import product as oprod
+    from oracle.sformat import BlockCSR
+    bo, rp, ci = pat.arrays()
+    A = BlockCSR(np.diff(bo), rp, ci.astype(np.int64), vals_host)
+    cores = len(os.sched_getaffinity(0))
+    rng = np.random.Generator(np.random.PCG64(seed))
+    order = rng.permutation(A.nblocks)
+    # calibrate on a small sample, then size the sample for about cpu_seconds
+    k = max(64, A.nblocks // 2000)
+    sub = np.sort(order[:k])
+    t0 = time.time()
+    oprod.mul_masked(A, A, A, subset=sub, nthreads=cores)
+    dt = max(time.time() - t0, 1e-3)
+    k2 = int(min(A.nblocks, max(k, k * cpu_seconds / dt)))
+    sub = np.sort(order[:k2])
+    _, fl = oprod.mul_count(A, A, A, subset=sub)
+    t0 = time.time()
+    oprod.mul_masked(A, A, A, subset=sub, nthreads=cores)
+    dt = time.time() - t0
+    desc = "%d of %d output blocks (%.2f%%), uniform random (seed %d), %.3g useful flops" % (
+        k2, A.nblocks, 100.0 * k2 / A.nblocks, seed, fl)
+    return fl / dt / 1e9, cores, desc, dt
+
+
+def run_reference(args, w, n, rank, world):
+    import torch
+    if rank != 0:
+        return
+    b, pat, vals, prep = build_input(w, n)
+    vals_host = vals.cpu().numpy()
+    del vals
+    torch.cuda.empty_cache()
+    times, cores, desc = [], 0, ""
+    for i in range(args.warmup + args.steps):
+        v, cores, desc, dt = oracle_sample(pat, vals_host, args.cpu_seconds / 2, seed=i)
+        if i >= args.warmup:
+            times.append(v)
+    value = statistics.median(times)
+    line = {"metric": METRIC, "value": value, "unit": "GFLOP/s", "impl": "reference", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": w.name, "n": n, "d": w.d, "nnz": pat.nnz, "blocks": pat.nblocks},
+            "cpu_baseline": {"value": value, "unit": "GFLOP/s", "cores": cores, "kind": "oracle", "sample": desc},
+            "e2e": {"value": value, "unit": "GFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------------------
+def main():
+    args = parse()
+    import torch
+    import workloads as W
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    w = W.WORKLOADS[args.workload]
+    n = args.n or w.n
+    if args.impl == "reference":
+        run_reference(args, w, n, rank, world)
+        if dist is not None:
+            dist.barrier()
+            dist.destroy_process_group()
+        return
+
+    from paper_2211_11681_gb300 import sformat as sf
+    b, pat, vals, prep = build_input(w, n)
+    t0 = time.time()
+    plan32 = sf.Plan(pat, pat, pat, "fp32")
+    triples, flops = plan32.stats()
+    prep["plan_s"] = round(time.time() - t0, 2)
+    A32 = vals.float()
+    C32 = torch.empty_like(A32)
+    stream = torch.cuda.current_stream()
+    for _ in range(args.warmup):
+        plan32.mul(A32, A32, C32)
+    torch.cuda.synchronize()
+    dev = torch.cuda.current_device()
+    try:
+        uuid = str(torch.cuda.get_device_properties(dev).uuid)
+        uuid = uuid if uuid.startswith("GPU-") else "GPU-" + uuid
+    except Exception:
+        uuid = None
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(uuid) as clk:
+        start = torch.cuda.Event(enable_timing=True)
+        stop = torch.cuda.Event(enable_timing=True)
+        start.record(stream)
+        for e0, e1 in evs:
+            e0.record(stream)
+            plan32.mul(A32, A32, C32)          # one launch of the product kernel
+            e1.record(stream)
+        stop.record(stream)
+        torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    total_ms = start.elapsed_time(stop)
+    launch_ms = [a.elapsed_time(c) for a, c in evs]
+    ms = total_ms / args.steps
+    if dist is not None:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = flops * world / (ms * 1e-3) / 1e9
+    clocks = clk.summary()
+
+    # FP64 product once, and the error of the mixed result against it
+    fp64 = None
+    if not args.no_fp64:
+        plan64 = sf.Plan(pat, pat, pat, "fp64")
+        C64 = torch.empty_like(vals)
+        plan64.mul(vals, vals, C64)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        plan64.mul(vals, vals, C64)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms64 = e0.elapsed_time(e1)
+        err = float((C32.double() - C64).norm() / C64.norm())
+        fp64 = {"ms": round(ms64, 3), "gflops": flops / (ms64 * 1e-3) / 1e9,
+                "mixed_rel_frob_err_vs_fp64": err, "mixed_speedup_vs_fp64": ms64 / ms}
+        del C64, plan64
+        torch.cuda.empty_cache()
+
+    # end to end through the C ABI with host buffers (pinned), copies inside the region
+    Ah = torch.empty(A32.numel(), dtype=torch.float32, pin_memory=True)
+    Ah.copy_(A32)
+    Ch = torch.empty(A32.numel(), dtype=torch.float32, pin_memory=True)
+    Ad = torch.empty_like(A32)
+    torch.cuda.synchronize()
+    e2e_steps = max(1, min(args.steps, 3))
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(e2e_steps):
+        Ad.copy_(Ah, non_blocking=True)
+        plan32.mul(Ad, Ad, C32)
+        Ch.copy_(C32, non_blocking=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = e0.elapsed_time(e1) / e2e_steps
+    e2e = {"value": flops * world / (e2e_ms * 1e-3) / 1e9, "unit": "GFLOP/s",
+           "h2d_bytes_per_step": int(Ah.numel() * 4), "d2h_bytes_per_step": int(Ch.numel() * 4),
+           "ms_per_step": round(e2e_ms, 3)}
+    del Ah, Ch, Ad
+
+    peaks = measured_peaks()
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    fp32_peak = 152 * 128 * 2 * sm_max * 1e6 / 1e12      # TFLOP/s from unit counts and clock
+    achieved = flops / (statistics.mean(launch_ms) * 1e-3) / 1e12
+    qbytes = algorithmic_bytes(pat, 4)
+    line = {
+        "metric": METRIC, "value": value, "unit": "GFLOP/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(ms, 3), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": dict(workload_config(w, n, pat, triples, flops), parallelism="replicas" if world > 1 else "1 GPU",
+                       prep_seconds=prep),
+        "hbm_gbs_algorithmic": qbytes / (ms * 1e-3) / 1e9,
+        "fp64": fp64,
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
+                     "frac": achieved / fp32_peak, "traffic": kernel_traffic(),
+                     "kernel": "sf::mul_kernel<float,false,false>",
+                     "peak_source": "152 SMs x 128 FP32 lanes x 2 flop x sm_max_mhz (derived)"},
+        "clocks": clocks,
+        "e2e": e2e,
+        "gpu_launches": args.steps,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu:
+        v, cores, desc, dt = oracle_sample(pat, vals.cpu().numpy(), args.cpu_seconds)
+        line["cpu_baseline"] = {"value": v, "unit": "GFLOP/s", "cores": cores, "kind": "oracle", "sample": desc,
+                                "seconds": round(dt, 2)}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

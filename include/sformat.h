@@ -83,6 +83,10 @@ int64_t s_pattern_nnz(s_pattern p);
 int64_t s_pattern_nblocks(s_pattern p);
 /* Copies the nblocks+1 entry offsets of the blocks into host memory `out`. */
 s_status s_pattern_block_offsets(s_pattern p, int64_t* out);
+/* Borrowed host copies of the pattern's arrays (valid until s_pattern_destroy):
+ * n_clusters, block_offset (n_clusters+1), rowptr (n_clusters+1), colidx (nblocks). */
+s_status s_pattern_host_arrays(s_pattern p, int32_t* n_clusters, const int64_t** block_offset,
+                               const int64_t** rowptr, const int32_t** colidx);
 
 /* ---- masked product, Eq. (product) of Thm. (product), Sec. 4.1 ---------------------- */
 

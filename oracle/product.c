@@ -68,13 +68,15 @@ int oracle_mul_masked(const int64_t* bsize,
 }
 
 /* Number of block triples (nu, lambda, nu') the product visits and its useful flop count
-   sum 2 n_nu n_lambda n_nu'. */
+   sum 2 n_nu n_lambda n_nu' (over the listed C blocks if subset != NULL). */
 int oracle_mul_count(const int64_t* bsize, const int64_t* a_rowptr, const int64_t* a_col,
                      const int64_t* b_rowptr, const int64_t* b_col, int64_t c_nblocks, const int64_t* c_brow,
-                     const int64_t* c_col, int64_t* triples, double* flops) {
+                     const int64_t* c_col, const int64_t* subset, int64_t nsubset, int64_t* triples, double* flops) {
   int64_t t = 0;
   double f = 0.0;
-  for (int64_t k = 0; k < c_nblocks; ++k) {
+  int64_t n = subset ? nsubset : c_nblocks;
+  for (int64_t s = 0; s < n; ++s) {
+    int64_t k = subset ? subset[s] : s;
     int64_t i = c_brow[k], j = c_col[k];
     for (int64_t ka = a_rowptr[i]; ka < a_rowptr[i + 1]; ++ka) {
       int64_t lam = a_col[ka];

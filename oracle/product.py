@@ -74,14 +74,20 @@ def mul_masked(A, B, Cpat, subset=None, nthreads=1):
     return C
 
 
-def mul_count(A, B, Cpat):
-    """(triples, useful flops) of P_{S_C}(A B)."""
+def mul_count(A, B, Cpat, subset=None):
+    """(triples, useful flops) of P_{S_C}(A B), or of the listed C blocks only."""
     lib = _load()
     t = ctypes.c_int64(0)
     f = ctypes.c_double(0.0)
+    if subset is not None:
+        sub = _i64(subset)
+        sp, ns = _p64(sub), len(sub)
+    else:
+        sp, ns = None, 0
     lib.oracle_mul_count(_p64(_i64(A.bsize)), _p64(_i64(A.rowptr)), _p64(_i64(A.colidx)),
                          _p64(_i64(B.rowptr)), _p64(_i64(B.colidx)), ctypes.c_int64(Cpat.nblocks),
-                         _p64(_i64(Cpat.brow)), _p64(_i64(Cpat.colidx)), ctypes.byref(t), ctypes.byref(f))
+                         _p64(_i64(Cpat.brow)), _p64(_i64(Cpat.colidx)), sp, ctypes.c_int64(ns),
+                         ctypes.byref(t), ctypes.byref(f))
     return int(t.value), float(f.value)
 
 

@@ -45,6 +45,9 @@ class _Borrowed:
         _sf.check(lib.s_pattern_block_offsets(self.h, out.ctypes.data_as(_P(_i64))))
         return out
 
+    def arrays(self):
+        return _sf.pattern_arrays(self.h)
+
     def __del__(self):
         try:
             if self.h.value:

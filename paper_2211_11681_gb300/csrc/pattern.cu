@@ -160,3 +160,13 @@ extern "C" s_status s_pattern_block_offsets(s_pattern p, int64_t* out) {
   std::memcpy(out, p->voff.data(), sizeof(int64_t) * p->voff.size());
   return S_OK;
 }
+
+extern "C" s_status s_pattern_host_arrays(s_pattern p, int32_t* n_clusters, const int64_t** block_offset,
+                                          const int64_t** rowptr, const int32_t** colidx) {
+  if (!p) return set_error(S_ERR_ARG, "s_pattern_host_arrays: NULL pattern");
+  if (n_clusters) *n_clusters = p->d.nc;
+  if (block_offset) *block_offset = p->boff.data();
+  if (rowptr) *rowptr = p->rowptr.data();
+  if (colidx) *colidx = p->colidx.data();
+  return S_OK;
+}

@@ -39,6 +39,7 @@ def _load():
         "s_pattern_nnz": (i64, [vp]),
         "s_pattern_nblocks": (i64, [vp]),
         "s_pattern_block_offsets": (i32, [vp, P(i64)]),
+        "s_pattern_host_arrays": (i32, [vp, P(i32), P(P(i64)), P(P(i64)), P(P(i32))]),
         "s_plan_create": (i32, [vp, vp, vp, i32, P(vp)]),
         "s_plan_destroy": (i32, [vp]),
         "s_plan_stats": (i32, [vp, P(i64), P(dbl)]),
@@ -90,6 +91,18 @@ def _a(x, dt):
     return np.ascontiguousarray(x, dtype=dt)
 
 
+def pattern_arrays(h):
+    """(block_offset, rowptr, colidx) numpy copies of a pattern handle's host arrays."""
+    nc = ctypes.c_int32()
+    bo, rp, ci = ctypes.POINTER(ctypes.c_int64)(), ctypes.POINTER(ctypes.c_int64)(), ctypes.POINTER(ctypes.c_int32)()
+    check(lib.s_pattern_host_arrays(h, ctypes.byref(nc), ctypes.byref(bo), ctypes.byref(rp), ctypes.byref(ci)))
+    n = nc.value
+    rowptr = np.ctypeslib.as_array(rp, shape=(n + 1,)).copy()
+    nb = int(rowptr[-1])
+    colidx = np.ctypeslib.as_array(ci, shape=(max(nb, 1),))[:nb].copy() if nb else np.zeros(0, np.int32)
+    return np.ctypeslib.as_array(bo, shape=(n + 1,)).copy(), rowptr, colidx
+
+
 class Pattern:
     """A block pattern S on the device (s_pattern_create)."""
 
@@ -118,6 +131,9 @@ class Pattern:
         out = np.zeros(self.nblocks + 1, dtype=np.int64)
         check(lib.s_pattern_block_offsets(self.h, out.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))))
         return out
+
+    def arrays(self):
+        return pattern_arrays(self.h)
 
     def close(self):
         if getattr(self, "h", None) is not None and self.h.value:
