@@ -127,6 +127,21 @@ s_status s_add(s_pattern p, s_prec prec, double alpha, const void* A, double bet
  * *lambda (the call synchronises the stream). */
 s_status s_norm_est(s_pattern p, const double* A, int iters, double* lambda, void* stream);
 
+/* Same estimate as s_norm_est, for callers that cannot allocate device memory during the
+ * call (for example an application whose device memory is owned entirely by its own pool
+ * allocator, or a latency-critical caller that must avoid cudaMalloc's device-wide
+ * synchronisation).  The paper has no counterpart: this is a deployment variant.
+ * It allocates nothing: its work vectors live in a static device array inside the library
+ * sized for matrix dimensions up to 1048576 (2 x 2^20 doubles + 2, about 16 MiB), which every
+ * GPU that loads the library holds until the process exits.  Larger patterns return
+ * S_ERR_ARG.  The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call before any stream
+ * capture.  All calls share the one array, which keeps the contents of the last call (the
+ * call clears what must start at zero): calls whose work overlaps on the GPU, on any
+ * streams, race and give undefined results.  The pattern and A stay caller-owned; the call
+ * synchronises the stream and writes the estimate to host *lambda. */
+s_status s_norm_est_noalloc(s_pattern p, const double* A, int iters, double* lambda, void* stream);
+
 typedef struct {
   int steps;          /* Newton-Schulz steps (S_SQRT); 0 = 25                              */
   int taylor_degree;  /* Taylor degree (S_EXP, S_EXP_NEG); 0 = 8                            */

@@ -47,6 +47,7 @@ def _load():
         "s_mul_masked_adjoint": (i32, [vp, vp, vp, vp, vp, vp, vp]),
         "s_add": (i32, [vp, i32, dbl, vp, dbl, vp, dbl, vp, vp]),
         "s_norm_est": (i32, [vp, vp, i32, P(dbl), vp]),
+        "s_norm_est_noalloc": (i32, [vp, vp, i32, P(dbl), vp]),
         "s_funm": (i32, [vp, i32, vp, vp, vp, vp]),
         "s_last_error": (ctypes.c_char_p, []),
         "s_version": (ctypes.c_char_p, []),
@@ -193,6 +194,13 @@ def add(pattern, A, B, C, alpha=1.0, beta=1.0, gamma=0.0, prec="fp64", stream=No
 def norm_est(pattern, A, iters=50, stream=None):
     lam = ctypes.c_double()
     check(lib.s_norm_est(pattern.h, _ptr(A), int(iters), ctypes.byref(lam), _stream(stream)))
+    return float(lam.value)
+
+
+def norm_est_noalloc(pattern, A, iters=50, stream=None):
+    """s_norm_est_noalloc: the same estimate with no device allocation during the call."""
+    lam = ctypes.c_double()
+    check(lib.s_norm_est_noalloc(pattern.h, _ptr(A), int(iters), ctypes.byref(lam), _stream(stream)))
     return float(lam.value)
 
 
