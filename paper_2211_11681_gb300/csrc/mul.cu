@@ -7,9 +7,7 @@
 // atomics).  The lambda set of a tile is the intersection of the sorted block-index lists
 // row(op(X), nu) and col(op(Y), nu'); a warp intersects them 32 entries of the X list at a
 // time by binary search in the Y list.  Warps take tiles from a device counter
-// (persistent grid sized to the SM count); tiles are ordered heaviest first.
-#include <cub/cub.cuh>
-
+// (persistent grid sized to the SM count); tiles follow the block order of S_C.
 #include <algorithm>
 #include <cstring>
 #include <new>
@@ -207,6 +205,199 @@ __global__ void __launch_bounds__(kWarps * 32) mul_kernel(MulArgs a, const T* __
   }
 }
 
+// Float product: one warp per output tile as above, with register micro-tiles and
+// double-buffered asynchronous staging.  Lane (mr, mc) of the first 25 lanes owns rows
+// 4mr..4mr+3 and columns 4mc..4mc+3 of the tile.  The warp first lists the matching
+// lambda blocks of a batch (a "stage" per kTile-wide slice of a lambda block), then streams
+// them: while stage s is multiplied out of shared memory, the copies of stage s+1 are in
+// flight (cp.async, 4-byte copies scatter op(X) transposed into sA[t][r], op(Y) lands in
+// sB[t][c]).  Each t step is one float4 load of each buffer and 16 FMAs.  Products are
+// summed in a float partial that is folded into the accumulator with an error-free
+// two-sum every kFold lambda blocks (compensated summation over lambda).
+constexpr int kF32Warps = 4;
+constexpr int kLd = kTile;       // 20: row length of sA / sB; float4 slots at 4*m are 16-byte aligned
+constexpr int kStages = 64;      // matching lambda blocks listed per batch
+constexpr int kFold = 4;         // lambda blocks per two-sum
+
+struct Stage {
+  int32_t bx, by;   // X and Y block ids
+  int16_t nl, t0;   // lambda block size, first t of this slice
+};
+
+__device__ __forceinline__ void cp_async4(float* dst, const float* src) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(d), "l"(src));
+}
+__device__ __forceinline__ void cp_async16(float* dst, const float* src) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(src));
+}
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;\n" ::); }
+template <int N>
+__device__ __forceinline__ void cp_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N));
+}
+
+template <bool TX, bool TY>
+__device__ __forceinline__ void stage_copy(const Stage& sg, const float* __restrict__ X, const float* __restrict__ Y,
+                                           const int64_t* xvoff, const int64_t* yvoff, int ni, int nj, int r0,
+                                           int c0, int th, int tw, int lane, float* xs, float* ys) {
+  const int nl = sg.nl, t0 = sg.t0;
+  const int tk = min(kTile, nl - t0);
+  const float* xb = X + xvoff[sg.bx];
+  const float* yb = Y + yvoff[sg.by];
+  const float rtk = 1.0f / (float)tk;
+  for (int e = lane; e < th * tk; e += 32) {
+    const int r = __float2int_rz(((float)e + 0.5f) * rtk), tt = e - r * tk;
+    const int gr = r0 + r, gt = t0 + tt;
+    cp_async4(xs + tt * kLd + r, TX ? xb + (int64_t)gt * ni + gr : xb + (int64_t)gr * nl + gt);
+  }
+  const bool vec = !TY && c0 == 0 && tw == nj && (nj & 3) == 0 && ((reinterpret_cast<uintptr_t>(yb) & 15) == 0);
+  if (vec) {
+    const float rnj = 1.0f / (float)nj;
+    for (int q = lane; q < (tk * nj) >> 2; q += 32) {
+      const int e = q << 2;
+      const int tt = __float2int_rz(((float)e + 0.5f) * rnj), c = e - tt * nj;
+      cp_async16(ys + tt * kLd + c, yb + (int64_t)(t0 + tt) * nj + c);
+    }
+  } else {
+    const float rtw = 1.0f / (float)tw;
+    for (int e = lane; e < tk * tw; e += 32) {
+      const int tt = __float2int_rz(((float)e + 0.5f) * rtw), c = e - tt * tw;
+      const int gt = t0 + tt, gc = c0 + c;
+      cp_async4(ys + tt * kLd + c, TY ? yb + (int64_t)gc * nl + gt : yb + (int64_t)gt * nj + gc);
+    }
+  }
+}
+
+template <bool TX, bool TY>
+__global__ void __launch_bounds__(kF32Warps * 32, 4) mul_f32_kernel(MulArgs a, const float* __restrict__ X,
+                                                                    const float* __restrict__ Y,
+                                                                    float* __restrict__ C) {
+  __shared__ __align__(16) float sA[kF32Warps][2][kTile * kLd];
+  __shared__ __align__(16) float sB[kF32Warps][2][kTile * kLd];
+  __shared__ Stage sStage[kF32Warps][kStages];  // the batch's matching lambda blocks
+  const int lane = threadIdx.x & 31;
+  const int w = threadIdx.x >> 5;
+  Stage* st = sStage[w];
+  const bool active = lane < 25;
+  const int mr = active ? lane / 5 : 0, mc = active ? lane % 5 : 0;
+  const int rl = 4 * mr, cl = 4 * mc;
+  for (;;) {
+    unsigned int t = 0;
+    if (lane == 0) t = atomicAdd(a.counter, 1u);
+    t = __shfl_sync(0xffffffffu, t, 0);
+    if (t >= a.ntiles) break;
+    const Tile tile = a.tiles[t];
+    const int k = tile.blk;
+    const int nu = a.c_brow[k], nup = a.c_col[k];
+    const int ni = a.bsize[nu], nj = a.bsize[nup];
+    const int th = min(kTile, ni - tile.r0), tw = min(kTile, nj - tile.c0);
+    float acc[16], comp[16], p[16];
+#pragma unroll
+    for (int q = 0; q < 16; ++q) acc[q] = comp[q] = p[q] = 0.0f;
+    int folded = 0;  // lambda blocks summed into p since the last two-sum
+    const int px1 = (int)a.x.ptr[nu + 1];
+    int px = (int)a.x.ptr[nu];
+    int py0 = (int)a.y.ptr[nup];
+    const int py1 = (int)a.y.ptr[nup + 1];
+    while (px < px1 && py0 < py1) {
+      // ---- list up to kStages matching lambda blocks ------------------------------------
+      int nm = 0;
+      while (px < px1 && py0 < py1 && nm <= kStages - 32) {
+        const int i = px + lane;
+        const int32_t lam = i < px1 ? __ldg(a.x.idx + i) : INT32_MAX;
+        const int pos = lower_bound_dev(a.y.idx, py0, py1, lam);
+        const bool hit = i < px1 && pos < py1 && __ldg(a.y.idx + pos) == lam;
+        const unsigned int mask = __ballot_sync(0xffffffffu, hit);
+        if (hit) {
+          const int kx = a.x.blk ? __ldg(a.x.blk + i) : i;
+          const int ky = a.y.blk ? __ldg(a.y.blk + pos) : pos;
+          const int o = nm + __popc(mask & ((1u << lane) - 1u));
+          st[o] = Stage{kx, ky, (int16_t)a.bsize[lam], 0};
+        }
+        nm += __popc(mask);
+        py0 = __shfl_sync(0xffffffffu, pos, 31);
+        px += 32;
+      }
+      __syncwarp();
+      if (nm == 0) continue;
+      // ---- stream the stages (lambda block m, slice q): copies of the next stage overlap
+      // the FMAs of the current one
+      int m = 0, q = 0;   // current stage
+      {
+        Stage sg = st[0];
+        stage_copy<TX, TY>(sg, X, Y, a.x.voff, a.y.voff, ni, nj, tile.r0, tile.c0, th, tw, lane, sA[w][0], sB[w][0]);
+        cp_commit();
+      }
+      int buf = 0;
+      for (;;) {
+        const Stage cur = st[m];
+        const int t0 = q * kTile;
+        const bool last_slice = t0 + kTile >= (int)cur.nl;
+        const int nm2 = last_slice ? m + 1 : m, nq2 = last_slice ? 0 : q + 1;
+        const bool more = nm2 < nm;
+        if (more) {
+          Stage sg = st[nm2];
+          sg.t0 = (int16_t)(nq2 * kTile);
+          stage_copy<TX, TY>(sg, X, Y, a.x.voff, a.y.voff, ni, nj, tile.r0, tile.c0, th, tw, lane, sA[w][buf ^ 1],
+                             sB[w][buf ^ 1]);
+          cp_commit();
+          cp_wait<1>();
+        } else {
+          cp_wait<0>();
+        }
+        __syncwarp();
+        const int tk = min(kTile, (int)cur.nl - t0);
+        if (active) {
+          const float* xs = sA[w][buf];
+          const float* ys = sB[w][buf];
+          for (int tt = 0; tt < tk; ++tt) {
+            const float4 av = *reinterpret_cast<const float4*>(xs + tt * kLd + rl);
+            const float4 bv = *reinterpret_cast<const float4*>(ys + tt * kLd + cl);
+            const float ar[4] = {av.x, av.y, av.z, av.w};
+            const float br[4] = {bv.x, bv.y, bv.z, bv.w};
+#pragma unroll
+            for (int ii = 0; ii < 4; ++ii)
+#pragma unroll
+              for (int jj = 0; jj < 4; ++jj) p[ii * 4 + jj] = fmaf(ar[ii], br[jj], p[ii * 4 + jj]);
+          }
+        }
+        __syncwarp();
+        if (last_slice && ++folded == kFold) {
+          folded = 0;
+#pragma unroll
+          for (int qq = 0; qq < 16; ++qq) {
+            const float hi = acc[qq] + p[qq];
+            const float bp = hi - acc[qq];
+            comp[qq] += (acc[qq] - (hi - bp)) + (p[qq] - bp);
+            acc[qq] = hi;
+            p[qq] = 0.0f;
+          }
+        }
+        if (!more) break;
+        m = nm2;
+        q = nq2;
+        buf ^= 1;
+      }
+    }
+    if (active) {
+      float* cb = C + a.c_voff[k];
+#pragma unroll
+      for (int ii = 0; ii < 4; ++ii)
+#pragma unroll
+        for (int jj = 0; jj < 4; ++jj) {
+          const int q = ii * 4 + jj;
+          const float hi = acc[q] + p[q];
+          const float bp = hi - acc[q];
+          const float err = (acc[q] - (hi - bp)) + (p[q] - bp);
+          const int r = rl + ii, c = cl + jj;
+          if (r < th && c < tw) cb[(int64_t)(tile.r0 + r) * nj + tile.c0 + c] = hi + (comp[q] + err);
+        }
+    }
+  }
+}
+
 static int g_sms = 0;
 static int num_sms() {
   if (!g_sms) {
@@ -239,12 +430,8 @@ s_status build_desc(const s_pattern_t* X, bool tx, const s_pattern_t* Y, bool ty
   unsigned long long* dtrip = nullptr;
   double* bflops = nullptr;
   int32_t* ntile = nullptr;
-  int32_t* order_in = nullptr;
   int32_t* order = nullptr;
-  double* keys_out = nullptr;
   int64_t* first = nullptr;
-  void* tmp = nullptr;
-  size_t tmp_bytes = 0, need = 0;
   s_status st = S_OK;
   cudaError_t e;
 #define TRY(call)                         \
@@ -259,9 +446,7 @@ s_status build_desc(const s_pattern_t* X, bool tx, const s_pattern_t* Y, bool ty
   TRY(cudaMemset(dtrip, 0, sizeof(unsigned long long)));
   TRY(cudaMalloc(&bflops, sizeof(double) * std::max<int64_t>(nb, 1)));
   TRY(cudaMalloc(&ntile, sizeof(int32_t) * std::max<int64_t>(nb, 1)));
-  TRY(cudaMalloc(&order_in, sizeof(int32_t) * std::max<int64_t>(nb, 1)));
   TRY(cudaMalloc(&order, sizeof(int32_t) * std::max<int64_t>(nb, 1)));
-  TRY(cudaMalloc(&keys_out, sizeof(double) * std::max<int64_t>(nb, 1)));
   TRY(cudaMalloc(&first, sizeof(int64_t) * (nb + 1)));
   TRY(cudaMalloc(&d.counter, sizeof(unsigned int)));
   if (nb > 0) {
@@ -273,16 +458,13 @@ s_status build_desc(const s_pattern_t* X, bool tx, const s_pattern_t* Y, bool ty
     int g = (int)((nb + 255) / 256);
     tile_count_kernel<<<g, 256>>>(C->d.bsize, C->d.brow, C->d.colidx, nb, ntile);
     TRY(cudaGetLastError());
-    // order blocks by useful flops, heaviest first
+    // tiles in block order: breadth-first block rows are spatially coherent, so warps that
+    // run at the same time share lambda blocks in L2; coarse (heavy) rows come first
     {
       std::vector<int32_t> iota(nb);
       for (int64_t k = 0; k < nb; ++k) iota[k] = (int32_t)k;
-      TRY(cudaMemcpy(order_in, iota.data(), sizeof(int32_t) * nb, cudaMemcpyHostToDevice));
+      TRY(cudaMemcpy(order, iota.data(), sizeof(int32_t) * nb, cudaMemcpyHostToDevice));
     }
-    TRY(cub::DeviceRadixSort::SortPairsDescending(nullptr, need, bflops, keys_out, order_in, order, (int)nb));
-    tmp_bytes = need;
-    TRY(cudaMalloc(&tmp, std::max<size_t>(tmp_bytes, 1)));
-    TRY(cub::DeviceRadixSort::SortPairsDescending(tmp, tmp_bytes, bflops, keys_out, order_in, order, (int)nb));
     // tiles per block in sorted order, exclusive scan -> first tile of each sorted block
     {
       std::vector<int32_t> nt(nb), ord(nb);
@@ -315,11 +497,8 @@ done:
   cudaFree(dtrip);
   cudaFree(bflops);
   cudaFree(ntile);
-  cudaFree(order_in);
   cudaFree(order);
-  cudaFree(keys_out);
   cudaFree(first);
-  cudaFree(tmp);
   if (st != S_OK) {
     free_desc(&d);
     return st;
@@ -351,13 +530,23 @@ static s_status launch_typed(const MulDesc& d, const void* X, const void* Y, voi
   if (d.ntiles == 0) return S_OK;
   SF_CUDA(cudaMemsetAsync(d.counter, 0, sizeof(unsigned int), st));
   int per_sm = 0;
-  auto kern = d.x.trans ? (d.y.trans ? mul_kernel<T, true, true> : mul_kernel<T, true, false>)
-                        : (d.y.trans ? mul_kernel<T, false, true> : mul_kernel<T, false, false>);
-  SF_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kWarps * 32, 0));
+  using K = void (*)(MulArgs, const T*, const T*, T*);
+  K kern;
+  int warps;
+  if constexpr (sizeof(T) == 4) {
+    kern = d.x.trans ? (d.y.trans ? mul_f32_kernel<true, true> : mul_f32_kernel<true, false>)
+                     : (d.y.trans ? mul_f32_kernel<false, true> : mul_f32_kernel<false, false>);
+    warps = kF32Warps;
+  } else {
+    kern = d.x.trans ? (d.y.trans ? mul_kernel<T, true, true> : mul_kernel<T, true, false>)
+                     : (d.y.trans ? mul_kernel<T, false, true> : mul_kernel<T, false, false>);
+    warps = kWarps;
+  }
+  SF_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, warps * 32, 0));
   if (per_sm < 1) per_sm = 1;
-  int64_t want = (d.ntiles + kWarps - 1) / kWarps;
+  int64_t want = (d.ntiles + warps - 1) / warps;
   int grid = (int)std::min<int64_t>(want, (int64_t)num_sms() * per_sm);
-  kern<<<grid, kWarps * 32, 0, st>>>(a, (const T*)X, (const T*)Y, (T*)C);
+  kern<<<grid, warps * 32, 0, st>>>(a, (const T*)X, (const T*)Y, (T*)C);
   SF_CUDA(cudaGetLastError());
   return S_OK;
 }
