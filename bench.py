@@ -47,6 +47,7 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="target CPU time of the oracle sample")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--batch", type=int, default=256, help="matrices of the batched workload")
     return ap.parse_args()
 
 
@@ -211,6 +212,86 @@ def run_reference(args, w, n, rank, world):
 
 
 # ---------------------------------------------------------------------------------------
+def run_batch(args, rank, world):
+    """256 independent matrices, N log-uniform in [2^10, 2^16], concatenated into one pattern:
+    one graph-replayed persistent launch per batched step, against a loop of one launch per
+    matrix (same kernel variant).  Metric: masked products per second."""
+    import torch
+    import workloads as W
+    from paper_2211_11681_gb300 import sformat as sf
+    from paper_2211_11681_gb300.builder import Builder
+    ws = W.batch_workloads(count=args.batch)
+    t0 = time.time()
+    pats, vals = [], []
+    for w in ws:
+        b = Builder(W.points(w), w.leaf, w.q, w.eta)
+        p, v = b.values(w.nu, w.ell, 1.0 / w.n, w.nugget, 0.0)
+        pats.append(p)
+        vals.append(v.float())
+        del b
+    prep = time.time() - t0
+    P = sf.concat(pats)
+    A = torch.cat(vals)
+    C = torch.empty_like(A)
+    plan = sf.Plan(P, P, P, "fp32")
+    triples, flops = plan.stats()
+    shape = plan.autotune(A, A, C)
+    g = plan.graph(A, A, C)
+    stream = torch.cuda.current_stream()
+    for _ in range(args.warmup):
+        g.launch()
+    torch.cuda.synchronize()
+    dev = torch.cuda.current_device()
+    try:
+        uuid = str(torch.cuda.get_device_properties(dev).uuid)
+        uuid = uuid if uuid.startswith("GPU-") else "GPU-" + uuid
+    except Exception:
+        uuid = None
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(uuid) as clk:
+        e0.record(stream)
+        for _ in range(args.steps):
+            g.launch()
+        e1.record(stream)
+        torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.steps
+    # one launch per matrix, same variant
+    plans, outs = [], []
+    for p in pats:
+        q = sf.Plan(p, p, p, "fp32")
+        q.set_variant(plan.variant_index)
+        plans.append(q)
+    for v in vals:
+        outs.append(torch.empty_like(v))
+    for _ in range(args.warmup):
+        for q, v, o in zip(plans, vals, outs):
+            q.mul(v, v, o)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(args.steps):
+        for q, v, o in zip(plans, vals, outs):
+            q.mul(v, v, o)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms_loop = e0.elapsed_time(e1) / args.steps
+    n = len(ws)
+    line = {"metric": "batched masked S-products/s (%d matrices, N log-uniform 2^10..2^16)" % n,
+            "value": n / (ms * 1e-3), "unit": "products/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": round(ms, 3), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "matern32_2d_batch", "matrices": n, "n_total": int(sum(w.n for w in ws)),
+                       "n_min": int(min(w.n for w in ws)), "n_max": int(max(w.n for w in ws)),
+                       "nnz": P.nnz, "blocks": P.nblocks, "triples": triples, "flops_per_step": flops,
+                       "prep_seconds": round(prep, 1), "l2": "inputs larger than L2, no flush"},
+            "gflops": flops / (ms * 1e-3) / 1e9, "autotuned_variant": shape,
+            "tune_ms": None,
+            "loop": {"ms_per_step": round(ms_loop, 3), "products_per_s": n / (ms_loop * 1e-3),
+                     "launches_per_step": n},
+            "batched_speedup_vs_loop": ms_loop / ms, "clocks": clk.summary(), "gpu_launches": args.steps}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     import torch
@@ -223,6 +304,12 @@ def main():
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    if args.workload == "matern32_2d_batch":
+        run_batch(args, rank, world)
+        if dist is not None:
+            dist.barrier()
+            dist.destroy_process_group()
+        return
     w = W.WORKLOADS[args.workload]
     n = args.n or w.n
     if args.impl == "reference":

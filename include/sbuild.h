@@ -59,12 +59,21 @@ s_status s_build_arrays(s_build b, const int64_t** block_offset, const int32_t**
  * samplet order, columns in original point order. */
 s_status s_build_dense_transform(s_build b, double* T);
 
+/* Samplet coordinates of a vector: out = T v for host v in original point order (the fast
+ * transform with the tree's two-scale matrices; host, O(n m_q)). */
+s_status s_build_transform(s_build b, const double* v, double* out);
+
 /* Values on the device.  nu in {0.5, 1.5, 2.5}, ell > 0.  On success *pattern is a new
  * pattern of the kept blocks (the caller destroys it) and the builder holds its
  * s_pattern_nnz(*pattern) values in device memory until s_build_take_values (or the next
  * s_build_values / s_build_destroy).  Uses the current device; synchronous. */
 s_status s_build_values(s_build b, double nu, double ell, double kscale, double nugget, double tau,
                         s_pattern* pattern);
+/* d/dell of the compressed values on a given pattern `on` (a sub-pattern of this builder's
+ * eta pattern, e.g. the kept pattern of s_build_values): P_on(T dK/dell T^T) times kscale,
+ * no nugget, no threshold, written to the caller's device buffer `out`
+ * (s_pattern_nnz(on) doubles).  Same device algorithm as s_build_values. */
+s_status s_build_values_dell(s_build b, double nu, double ell, double kscale, s_pattern on, double* out);
 /* Copies the held values into the caller's device buffer `dst` (s_pattern_nnz doubles)
  * on `stream`, waits for the copy, and releases the builder's copy. */
 s_status s_build_take_values(s_build b, double* dst, void* stream);

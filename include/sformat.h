@@ -88,6 +88,13 @@ s_status s_pattern_block_offsets(s_pattern p, int64_t* out);
 s_status s_pattern_host_arrays(s_pattern p, int32_t* n_clusters, const int64_t** block_offset,
                                const int64_t** rowptr, const int32_t** colidx);
 
+/* Batching: one pattern that holds `count` independent matrices side by side (block
+ * diagonal in the union of their clusters, each part from its own tree).  The value buffer
+ * of the result is the concatenation of the parts' value buffers in order, so one masked
+ * product on the result computes all the parts' products in one launch.  The parts may be
+ * destroyed afterwards. */
+s_status s_pattern_concat(int32_t count, const s_pattern* parts, s_pattern* out);
+
 /* ---- masked product, Eq. (product) of Thm. (product), Sec. 4.1 ---------------------- */
 
 /* Symbolic phase of C = P_{S_C}(A B): checks that the three patterns share one tree,
@@ -98,6 +105,18 @@ s_status s_plan_create(s_pattern A, s_pattern B, s_pattern C, s_prec prec, s_pla
 s_status s_plan_destroy(s_plan plan);
 /* Exact triple count and useful flop count of the plan's product. */
 s_status s_plan_stats(s_plan plan, int64_t* triples, double* flops);
+/* Autotuner of S_FP32 plans: times every float kernel variant (output tile edge and the
+ * micro-tile of one lane) on the given operands, three launches each after one warm-up,
+ * and keeps the fastest for this plan's forward product.  C is overwritten.  *chosen
+ * (optional) receives the variant index.  S_FP64 plans have one shape (no-op).
+ * Synchronises the stream. */
+s_status s_plan_autotune(s_plan plan, const void* A, const void* B, void* C, void* stream, int* chosen);
+/* Selects float variant `variant` (0 .. s_plan_num_variants()-1) for the plan's forward
+ * product by hand (S_FP32 plans only). */
+s_status s_plan_set_variant(s_plan plan, int variant);
+int s_plan_num_variants(void);
+/* Shape of a float variant (variant < 0: the plan's current one): tile edge and micro-tile. */
+s_status s_plan_variant(s_plan plan, int variant, int* tile, int* micro_rows, int* micro_cols);
 
 /* C = P_{S_C}(A B): for every block (nu, nu') of S_C,
  *   C(nu, nu') = sum over lambda with (nu,lambda) in S_A and (lambda,nu') in S_B of
@@ -111,6 +130,14 @@ s_status s_mul_masked(s_plan plan, const void* A, const void* B, void* C, void* 
  * Either output may be NULL to skip it.  Same element type as the plan. */
 s_status s_mul_masked_adjoint(s_plan plan, const void* dC, const void* A, const void* B, void* dA, void* dB,
                               void* stream);
+
+/* CUDA graph of one s_mul_masked call on fixed buffers: captured on a private stream and
+ * instantiated once; s_graph_launch replays it on any stream.  The plan and the buffers
+ * must outlive the graph. */
+typedef struct s_graph_t* s_graph;
+s_status s_graph_capture_mul(s_plan plan, const void* A, const void* B, void* C, s_graph* out);
+s_status s_graph_launch(s_graph g, void* stream);
+s_status s_graph_destroy(s_graph g);
 
 /* ---- addition, Sec. 4.1 ---------------------------------------------------------------- */
 
@@ -150,7 +177,11 @@ typedef struct {
                          S_EXP*: lambda used for the squaring count (0 = norm estimate)     */
   int squarings;      /* S_EXP*: -1 = from lambda, else forced count                        */
   double* residual;   /* optional host out: S_SQRT residual ||P_S(X X) - A||_F / ||A||_F    */
-  void* checkpoints;  /* optional device buffer of 2*steps*nnz doubles: (Y_k, Z_k) per step */
+  void* checkpoints;  /* optional device buffer of 2*steps*nnz doubles: (Y_k, Z_k) per step
+                         (S_FP64 only)                                                      */
+  int refine;         /* S_SQRT: residual-correction steps in double after the iteration:
+                         R = A/c - P_S(Y Y), Y <- Y + P_S(Z R)/2 (Newton's method for
+                         Y^2 = A/c with Z standing in for Y^{-1}); 0 = none               */
 } s_funm_opts;
 
 /* F = f(A) on A's pattern, every product masked to that pattern (the pattern must hold
@@ -160,9 +191,27 @@ typedef struct {
  *              F = sqrt(c) Y_steps.
  *   S_EXP, S_EXP_NEG   exp(+-A) by the power series of Sec. 4.4 truncated at the Taylor
  *              degree, Horner's rule on X = +-A/2^s, then s masked squarings,
- *              s = max(0, ceil(log2(lambda/0.5))).
+ *              s = max(0, ceil(log2(lambda/0.5))).  With prec S_FP32 the Horner products
+ *              run in float and the squarings in double.
  * Synchronises the stream once (norm estimate) unless opts->scale is given. */
 s_status s_funm(s_pattern p, s_fn fn, const double* A, double* F, const s_funm_opts* opts, void* stream);
+
+/* Reverse mode of S_SQRT (coupled Newton-Schulz, same recurrences as s_funm) with the
+ * scaling c frozen: given dF = dL/dF on A's pattern and the per-step checkpoints
+ * (Y_k, Z_k), k = 0..steps-1, that s_funm wrote into opts->checkpoints (2*steps*nnz
+ * doubles), writes dA = dL/dA on A's pattern.  Each step replays P = P_S(Z_k Y_k) and
+ * T_k = (3I - P)/2 and applies the adjoints of Y' = P_S(Y T), Z' = P_S(T Z) and
+ * P = P_S(Z Y), each a pair of masked products (see s_mul_masked_adjoint).  Double
+ * buffers; prec S_FP64.  Allocates its work buffers; synchronises the stream. */
+s_status s_funm_sqrt_backward(s_pattern p, int steps, double c, const double* checkpoints, const double* dF,
+                              double* dA, void* stream);
+
+/* Loss of the differentiation checks: *out (host) = z^T X z = sum over the blocks (nu, nu') of
+ * the pattern of z_nu^T X(nu, nu') z_nu', with z a device vector of the pattern's dimension in
+ * samplet coordinates (fixed-order reduction; synchronises the stream). */
+s_status s_quad_form(s_pattern p, const double* X, const double* z, double* out, void* stream);
+/* Its gradient: dX(nu, nu') = z_nu z_nu'^T on every block of the pattern. */
+s_status s_quad_form_grad(s_pattern p, const double* z, double* dX, void* stream);
 
 /* ---- diagnostics ------------------------------------------------------------------------ */
 const char* s_last_error(void);

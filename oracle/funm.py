@@ -10,7 +10,10 @@ Test infrastructure only (see ``oracle/__init__``).
                  by a contour integral with selected inversion, Sec. 4.4; this is the
                  product-only method: Y_0 = A/c, Z_0 = I, T_k = (3I - Z_k Y_k)/2,
                  Y_{k+1} = Y_k T_k, Z_{k+1} = T_k Z_k, X = sqrt(c) Y_K), every product masked
-                 to S.  Reading: c = 1.01 * norm_estimate(A), frozen.
+                 to S.  Reading: c = 1.01 * norm_estimate(A), frozen.  Optional residual
+                 correction after the iteration (Newton's method for Y^2 = A/c with the
+                 inverse of Y replaced by the coupled iterate Z ~ (A/c)^{-1/2}):
+                 R = A/c - P_S(Y Y), Y <- Y + P_S(Z R)/2, repeated `refine` times.
   expm_taylor    exp(sign * A) by the power series of Sec. 4.4, truncated at degree 8
                  (Sec. 5.3 finds stagnation after 8 terms), evaluated by Horner's rule on
                  X = sign*A/2^s, then s masked squarings.  Reading: s = max(0,
@@ -51,7 +54,7 @@ def norm_estimate(A, iters=50):
     return lam
 
 
-def sqrtm_ns(A, steps=25, c=None, return_history=False, nthreads=1):
+def sqrtm_ns(A, steps=25, c=None, return_history=False, nthreads=1, refine=0):
     """Returns X (and, with return_history, the list of (Y_k, Z_k) and c)."""
     if c is None:
         c = 1.01 * norm_estimate(A)
@@ -65,6 +68,10 @@ def sqrtm_ns(A, steps=25, c=None, return_history=False, nthreads=1):
         Yn = _prod.mul_masked(Y, T, A, nthreads=nthreads)
         Zn = _prod.mul_masked(T, Z, A, nthreads=nthreads)
         Y, Z = Yn, Zn
+    B = A.like(A.val / c)
+    for _ in range(refine):
+        R = add(B, _prod.mul_masked(Y, Y, A, nthreads=nthreads), 1.0, -1.0)
+        Y = add(Y, _prod.mul_masked(Z, R, A, nthreads=nthreads), 1.0, 0.5)
     X = A.like(math.sqrt(c) * Y.val)
     if return_history:
         return X, hist, c

@@ -20,6 +20,8 @@ for _name, (_res, _args) in {
     "s_build_dense_transform": (_i32, [_vp, _P(_dbl)]),
     "s_build_values": (_i32, [_vp, _dbl, _dbl, _dbl, _dbl, _dbl, _P(_vp)]),
     "s_build_take_values": (_i32, [_vp, _vp, _vp]),
+    "s_build_values_dell": (_i32, [_vp, _dbl, _dbl, _dbl, _vp, _vp]),
+    "s_build_transform": (_i32, [_vp, _P(_dbl), _P(_dbl)]),
 }.items():
     _f = getattr(lib, _name)
     _f.restype = _res
@@ -96,6 +98,21 @@ class Builder:
         out = torch.empty(max(pat.nnz, 1), dtype=torch.float64, device="cuda")
         _sf.check(lib.s_build_take_values(self.h, _vp(out.data_ptr()), _sf._stream(None)))
         return pat, out[:pat.nnz]
+
+    def values_dell(self, pattern, nu, ell, kscale=1.0):
+        """d/dell of the compressed values on `pattern` (torch float64 CUDA tensor)."""
+        import torch
+        out = torch.empty(max(pattern.nnz, 1), dtype=torch.float64, device="cuda")
+        _sf.check(lib.s_build_values_dell(self.h, float(nu), float(ell), float(kscale), pattern.h,
+                                          _vp(out.data_ptr())))
+        return out[:pattern.nnz]
+
+    def transform(self, v):
+        """T v (samplet coordinates) of a host vector in original point order."""
+        v = np.ascontiguousarray(v, dtype=np.float64)
+        out = np.zeros(self.n)
+        _sf.check(lib.s_build_transform(self.h, v.ctypes.data_as(_P(_dbl)), out.ctypes.data_as(_P(_dbl))))
+        return out
 
     def __del__(self):
         try:

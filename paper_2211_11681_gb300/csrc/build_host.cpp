@@ -411,3 +411,32 @@ extern "C" s_status s_build_dense_transform(s_build b, double* T) {
   for (int64_t g = 0; g < n; ++g) std::memcpy(T + (size_t)g * n, &W[(size_t)b->rowslot[g] * n], sizeof(double) * n);
   return S_OK;
 }
+
+extern "C" s_status s_build_transform(s_build b, const double* v, double* out) {
+  if (!b || !v || !out) return set_error(S_ERR_ARG, "s_build_transform: NULL argument");
+  const int64_t n = b->n;
+  // tree order, then the in-place two-scale transform level by level (bottom-up)
+  std::vector<double> w(n);
+  for (int64_t i = 0; i < n; ++i) w[i] = v[b->perm[i]];
+  const int nc = (int)b->cl.size();
+  std::vector<std::vector<int32_t>> bylevel(b->depth + 1);
+  for (int i = 0; i < nc; ++i) bylevel[b->cl[i].level].push_back(i);
+  std::vector<double> in, o;
+  for (int lev = b->depth; lev >= 0; --lev)
+    for (int id : bylevel[lev]) {
+      const BCluster& c = b->cl[id];
+      const int32_t* sl = b->slots.data() + b->slot_off[id];
+      const int m = c.nin;
+      in.assign(m, 0.0);
+      o.assign(m, 0.0);
+      for (int i = 0; i < m; ++i) in[i] = w[sl[i]];
+      for (int j = 0; j < m; ++j) {
+        double acc = 0.0;
+        for (int i = 0; i < m; ++i) acc += c.Q[(size_t)i * m + j] * in[i];
+        o[j] = acc;
+      }
+      for (int j = 0; j < m; ++j) w[sl[j]] = o[j];
+    }
+  for (int64_t g = 0; g < n; ++g) out[g] = w[b->rowslot[g]];
+  return S_OK;
+}

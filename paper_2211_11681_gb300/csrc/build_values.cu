@@ -38,7 +38,19 @@ struct Geo {
 };
 
 __device__ __forceinline__ float matern(float r, int p, float inv_ell, float scale) {
-  // half-integer closed form, Sec. 2: nu = p + 1/2
+  // half-integer closed form, Sec. 2: nu = p + 1/2; p >= 3 encodes d/dell of nu = (p-3) + 1/2
+  if (p >= 3) {
+    // kappa = f(t), t = sqrt(2 nu) r / ell, dkappa/dell = -f'(t) t / ell
+    const int q = p - 3;
+    const float a = q == 0 ? 1.0f : (q == 1 ? 1.7320508075688772f : 2.23606797749979f);
+    const float t = a * r * inv_ell;
+    const float e = __expf(-t);
+    float g;  // -f'(t) * t
+    if (q == 0) g = t * e;
+    else if (q == 1) g = t * t * e;
+    else g = t * t * (1.0f + t) * (1.0f / 3.0f) * e;
+    return scale * g * inv_ell;
+  }
   if (p == 0) return scale * __expf(-r * inv_ell);
   if (p == 1) {
     const float t = 1.7320508075688772f * r * inv_ell;
@@ -234,19 +246,19 @@ using namespace sf;
 
 s_build_t::~s_build_t() { cudaFree(dvals); }
 
-extern "C" s_status s_build_values(s_build b, double nu, double ell, double kscale, double nugget, double tau,
-                                   s_pattern* pattern) {
-  if (!b || !pattern) return set_error(S_ERR_ARG, "s_build_values: NULL argument");
-  *pattern = nullptr;
-  cudaFree(b->dvals);
-  b->dvals = nullptr;
-  b->nvals = 0;
+// Values of the kernel (deriv = false) or of its ell-derivative (deriv = true).  Without a
+// given pattern the kept pattern is decided by tau and returned in *pattern with the values
+// held by the builder; with a given pattern (a sub-pattern of the eta pattern) the values on
+// it are written to `out` (no threshold, no nugget).
+static s_status values_impl(s_build b, double nu, double ell, double kscale, double nugget, double tau, bool deriv,
+                            const s_pattern_t* given, double* out, s_pattern* pattern) {
   int p;
   if (std::fabs(nu - 0.5) < 1e-12) p = 0;
   else if (std::fabs(nu - 1.5) < 1e-12) p = 1;
   else if (std::fabs(nu - 2.5) < 1e-12) p = 2;
   else return set_error(S_ERR_ARG, "s_build_values: nu must be 0.5, 1.5 or 2.5");
   if (!(ell > 0.0)) return set_error(S_ERR_ARG, "s_build_values: ell must be positive");
+  if (deriv) p += 3;
   const int64_t n = b->n;
   const int nc = (int)b->cl.size();
   for (const auto& c : b->cl)
@@ -526,66 +538,105 @@ extern "C" s_status s_build_values(s_build b, double nu, double ell, double ksca
   }
   for (auto& s : stack) cudaFree(s.second);
   SF_CUDA(cudaDeviceSynchronize());
-  // ---- kept pattern (decided per unordered pair) ---------------------------------------
+  // ---- kept pattern (decided per unordered pair), or the given one ----------------------
   std::vector<float> bmax(nut);
   SF_CUDA(cudaMemcpy(bmax.data(), dbmax, sizeof(float) * nut, cudaMemcpyDeviceToHost));
+  auto pair_source = [&](int a, int c) -> int64_t {  // upper-triangle id of {a, c}, or -1
+    const int lo = std::min(a, c), hi = std::max(a, c);
+    const int32_t* beg = ci.data() + rp[lo];
+    const int32_t* end = ci.data() + rp[lo + 1];
+    const int32_t* pos = std::lower_bound(beg, end, hi);
+    if (pos == end || *pos != hi) return -1;
+    return ut_id[rp[lo] + (pos - beg)];
+  };
   std::vector<int64_t> krp(nc + 1, 0);
-  std::vector<int32_t> kci, kbrow;
+  std::vector<int32_t> kci;
   std::vector<int64_t> ksrc;
-  for (int a = 0; a < nc; ++a) {
-    for (int64_t k = rp[a]; k < rp[a + 1]; ++k) {
-      const int c = ci[k];
-      int64_t kab;
-      if (c >= a) {
-        kab = k;
-      } else {
-        const int32_t* beg = ci.data() + rp[c];
-        const int32_t* end = ci.data() + rp[c + 1];
-        const int32_t* pos = std::lower_bound(beg, end, a);
-        if (pos == end || *pos != a) continue;
-        kab = rp[c] + (pos - beg);
-      }
-      const int32_t u = ut_id[kab];
-      if (u < 0) continue;
-      if (a == c || (double)bmax[u] >= tau) {
+  if (given) {
+    if (given->d.nc != nc) return set_error(S_ERR_MISMATCH, "s_build_values_dell: pattern from another tree");
+    for (int a = 0; a < nc; ++a) {
+      for (int64_t k = given->rowptr[a]; k < given->rowptr[a + 1]; ++k) {
+        const int c = given->colidx[k];
+        const int64_t u = pair_source(a, c);
+        if (u < 0) return set_error(S_ERR_PATTERN, "s_build_values_dell: block outside the eta pattern");
         kci.push_back(c);
-        kbrow.push_back(a);
         ksrc.push_back(ut_off[u]);
       }
+      krp[a + 1] = (int64_t)kci.size();
     }
-    krp[a + 1] = (int64_t)kci.size();
+  } else {
+    for (int a = 0; a < nc; ++a) {
+      for (int64_t k = rp[a]; k < rp[a + 1]; ++k) {
+        const int c = ci[k];
+        const int64_t u = pair_source(a, c);
+        if (u < 0) continue;
+        if (a == c || (double)bmax[u] >= tau) {
+          kci.push_back(c);
+          ksrc.push_back(ut_off[u]);
+        }
+      }
+      krp[a + 1] = (int64_t)kci.size();
+    }
   }
   s_pattern pat = nullptr;
-  if ((st = s_pattern_create(nc, b->block_offset.data(), b->level.data(), krp.data(), kci.data(), &pat))) return st;
-  const int64_t nnz = s_pattern_nnz(pat);
-  double* vals = nullptr;
-  cudaError_t e = cudaMalloc(&vals, sizeof(double) * std::max<int64_t>(nnz, 1));
-  if (e != cudaSuccess) {
-    s_pattern_destroy(pat);
-    return cuda_error(e, "cudaMalloc(values)");
+  const s_pattern_t* tgt = given;
+  if (!given) {
+    if ((st = s_pattern_create(nc, b->block_offset.data(), b->level.data(), krp.data(), kci.data(), &pat))) return st;
+    tgt = pat;
+  }
+  const int64_t nnz = tgt->d.nnz;
+  double* vals = out;
+  if (!given) {
+    cudaError_t e = cudaMalloc(&vals, sizeof(double) * std::max<int64_t>(nnz, 1));
+    if (e != cudaSuccess) {
+      s_pattern_destroy(pat);
+      return cuda_error(e, "cudaMalloc(values)");
+    }
   }
   int64_t* dsrc;
   if ((st = upload(&dsrc, ksrc))) {
-    s_pattern_destroy(pat);
-    cudaFree(vals);
+    if (!given) {
+      s_pattern_destroy(pat);
+      cudaFree(vals);
+    }
     return st;
   }
   fr.add(dsrc);
   const int64_t nk = (int64_t)kci.size();
   if (nk)
-    assemble_kernel<<<(unsigned)((nk * 32 + 255) / 256), 256>>>(nk, pat->d.brow, pat->d.colidx, pat->d.voff, dsrc,
-                                                              dbsize, dstage, nugget, tau, vals);
-  e = cudaGetLastError();
+    assemble_kernel<<<(unsigned)((nk * 32 + 255) / 256), 256>>>(nk, tgt->d.brow, tgt->d.colidx, tgt->d.voff, dsrc,
+                                                              dbsize, dstage, given ? 0.0 : nugget,
+                                                              given ? 0.0 : tau, vals);
+  cudaError_t e = cudaGetLastError();
   if (e == cudaSuccess) e = cudaDeviceSynchronize();
   if (e != cudaSuccess) {
-    s_pattern_destroy(pat);
-    cudaFree(vals);
+    if (!given) {
+      s_pattern_destroy(pat);
+      cudaFree(vals);
+    }
     return cuda_error(e, "assemble_kernel");
   }
-  *pattern = pat;
-  b->dvals = vals;
-  b->nvals = nnz;
+  if (!given) {
+    *pattern = pat;
+    b->dvals = vals;
+    b->nvals = nnz;
+  }
   return S_OK;
+}
+
+extern "C" s_status s_build_values(s_build b, double nu, double ell, double kscale, double nugget, double tau,
+                                   s_pattern* pattern) {
+  if (!b || !pattern) return set_error(S_ERR_ARG, "s_build_values: NULL argument");
+  *pattern = nullptr;
+  cudaFree(b->dvals);
+  b->dvals = nullptr;
+  b->nvals = 0;
+  return values_impl(b, nu, ell, kscale, nugget, tau, false, nullptr, nullptr, pattern);
+}
+
+extern "C" s_status s_build_values_dell(s_build b, double nu, double ell, double kscale, s_pattern on, double* out) {
+  if (!b || !on || (!out && on->d.nnz > 0)) return set_error(S_ERR_ARG, "s_build_values_dell: NULL argument");
+  return values_impl(b, nu, ell, kscale, 0.0, 0.0, true, on, out, nullptr);
 }
 
 extern "C" s_status s_build_take_values(s_build b, double* dst, void* stream) {

@@ -76,8 +76,10 @@ struct MulDesc {
   const s_pattern_t* pc;
   const s_pattern_t* px;
   const s_pattern_t* py;
-  Tile* tiles = nullptr;     // device tile list, heaviest first
+  Tile* tiles = nullptr;     // device tile list, block order
   int64_t ntiles = 0;
+  int edge = 20;             // tile edge of the list
+  int variant = 0;           // float kernel variant (autotuned)
   unsigned int* counter = nullptr;  // device work counter
   int64_t triples = 0;
   double flops = 0.0;
@@ -106,4 +108,5 @@ struct s_plan_t {
   sf::MulDesc adjA;  // dA = P_{S_A}(dC B^T), built on first use
   sf::MulDesc adjB;  // dB = P_{S_B}(A^T dC)
   bool adj_built = false;
+  float tune_ms[8] = {0};
 };

@@ -59,6 +59,41 @@ __global__ void dist_to_identity_kernel(int64_t nnz, const T* __restrict__ v, in
   if (threadIdx.x == 0) *out = red[0] + n;
 }
 
+// part[k] = z_nu^T X(nu, nu') z_nu' for block k = (nu, nu')
+__global__ void quad_part_kernel(int64_t nb, const int32_t* brow, const int32_t* bcol, const int32_t* bsize,
+                                 const int64_t* boff, const int64_t* voff, const double* X, const double* z,
+                                 double* part) {
+  const int lane = threadIdx.x & 31;
+  const int64_t k = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  if (k >= nb) return;
+  const int i = brow[k], j = bcol[k];
+  const int ni = bsize[i], nj = bsize[j];
+  const double* x = X + voff[k];
+  const double* zi = z + boff[i];
+  const double* zj = z + boff[j];
+  double s = 0.0;
+  for (int e = lane; e < ni * nj; e += 32) {
+    const int r = e / nj, c = e - r * nj;
+    s = fma(zi[r] * x[e], zj[c], s);
+  }
+  for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if (lane == 0) part[k] = s;
+}
+
+// dX(nu, nu') = z_nu z_nu'^T on every block of the pattern
+__global__ void quad_grad_kernel(int64_t nb, const int32_t* brow, const int32_t* bcol, const int32_t* bsize,
+                                 const int64_t* boff, const int64_t* voff, const double* z, double* dX) {
+  const int lane = threadIdx.x & 31;
+  const int64_t k = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  if (k >= nb) return;
+  const int i = brow[k], j = bcol[k];
+  const int ni = bsize[i], nj = bsize[j];
+  for (int e = lane; e < ni * nj; e += 32) {
+    const int r = e / nj, c = e - r * nj;
+    dX[voff[k] + e] = z[boff[i] + r] * z[boff[j] + c];
+  }
+}
+
 template <typename S, typename D>
 __global__ void convert_kernel(int64_t n, const S* a, D* b, double scale) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
@@ -160,6 +195,7 @@ extern "C" s_status s_funm(s_pattern p, s_fn fn, const double* A, double* F, con
     if ((s = run_add(p, prec, 1.0 / c, Ain, 0.0, nullptr, 0.0, Y, st))) return s;
     SF_CUDA(cudaMemsetAsync(Z, 0, w * nnz, st));
     if ((s = run_add(p, prec, 1.0, Z, 0.0, nullptr, 1.0, Z, st))) return s;
+    const int refine = std::max(0, o.refine);
     for (int k = 0; k < steps; ++k) {
       if (o.checkpoints && prec == S_FP64) {
         double* ck = (double*)o.checkpoints + (int64_t)2 * k * nnz;
@@ -180,11 +216,42 @@ extern "C" s_status s_funm(s_pattern p, s_fn fn, const double* A, double* F, con
       std::swap(Z, P);
     }
     const double sc = std::sqrt(c);
-    if (prec == S_FP64) {
-      if ((s = run_add(p, prec, sc, Y, 0.0, nullptr, 0.0, F, st))) return s;
+    if (refine == 0) {
+      if (prec == S_FP64) {
+        if ((s = run_add(p, prec, sc, Y, 0.0, nullptr, 0.0, F, st))) return s;
+      } else {
+        convert_kernel<float, double><<<g, 256, 0, st>>>(nnz, (const float*)Y, F, sc);
+        SF_CUDA(cudaGetLastError());
+      }
     } else {
-      convert_kernel<float, double><<<g, 256, 0, st>>>(nnz, (const float*)Y, F, sc);
-      SF_CUDA(cudaGetLastError());
+      // residual correction in double (Newton's method for Y^2 = A/c with the inverse of Y
+      // replaced by the coupled iterate Z):  R = A/c - P_S(Y Y),  Y <- Y + P_S(Z R)/2
+      s_plan p64 = nullptr;
+      if ((s = s_plan_create(p, p, p, S_FP64, &p64))) return s;
+      PlanGuard pg64{p64};
+      DevBuf dY, dZ, dR, dW;
+      const size_t b8 = sizeof(double) * nnz + 16;
+      SF_CUDA(cudaMalloc(&dY.p, b8));
+      SF_CUDA(cudaMalloc(&dZ.p, b8));
+      SF_CUDA(cudaMalloc(&dR.p, b8));
+      SF_CUDA(cudaMalloc(&dW.p, b8));
+      SyncOnExit sync64{st};
+      double *Y8 = (double*)dY.p, *Z8 = (double*)dZ.p, *R8 = (double*)dR.p, *W8 = (double*)dW.p;
+      if (prec == S_FP64) {
+        SF_CUDA(cudaMemcpyAsync(Y8, Y, b8 - 16, cudaMemcpyDeviceToDevice, st));
+        SF_CUDA(cudaMemcpyAsync(Z8, Z, b8 - 16, cudaMemcpyDeviceToDevice, st));
+      } else {
+        convert_kernel<float, double><<<g, 256, 0, st>>>(nnz, (const float*)Y, Y8, 1.0);
+        convert_kernel<float, double><<<g, 256, 0, st>>>(nnz, (const float*)Z, Z8, 1.0);
+      }
+      for (int r = 0; r < refine; ++r) {
+        if ((s = run_mul(p64->fwd, S_FP64, Y8, Y8, W8, st))) return s;                 // W = P_S(Y Y)
+        if ((s = run_add(p, S_FP64, 1.0 / c, A, -1.0, W8, 0.0, R8, st))) return s;     // R = A/c - W
+        if ((s = run_mul(p64->fwd, S_FP64, Z8, R8, W8, st))) return s;                 // W = P_S(Z R)
+        if ((s = run_add(p, S_FP64, 1.0, Y8, 0.5, W8, 0.0, Y8, st))) return s;         // Y += W/2
+      }
+      if ((s = run_add(p, S_FP64, sc, Y8, 0.0, nullptr, 0.0, F, st))) return s;
+      SF_CUDA(cudaStreamSynchronize(st));
     }
     // divergence: ||T_k - I||_F grew by more than 1.5x on two consecutive steps
     {
@@ -242,18 +309,116 @@ extern "C" s_status s_funm(s_pattern p, s_fn fn, const double* A, double* F, con
       if ((s = run_mul(plan->fwd, prec, X, E, W, st))) return s;                   // W = P_S(X E)
       if ((s = run_add(p, prec, 1.0 / k, W, 0.0, nullptr, 1.0, E, st))) return s; // E = I + W/k
     }
-    for (int r = 0; r < sq; ++r) {
-      if ((s = run_mul(plan->fwd, prec, E, E, W, st))) return s;                   // E = P_S(E E)
-      std::swap(E, W);
-    }
     if (prec == S_FP64) {
+      for (int r = 0; r < sq; ++r) {
+        if ((s = run_mul(plan->fwd, prec, E, E, W, st))) return s;                 // E = P_S(E E)
+        std::swap(E, W);
+      }
       SF_CUDA(cudaMemcpyAsync(F, E, w * nnz, cudaMemcpyDeviceToDevice, st));
     } else {
+      // float Horner, double squarings: E (float) -> F, then F = P_S(F F) s times
       convert_kernel<float, double><<<g, 256, 0, st>>>(nnz, (const float*)E, F, 1.0);
       SF_CUDA(cudaGetLastError());
+      if (sq > 0) {
+        s_plan p64 = nullptr;
+        if ((s = s_plan_create(p, p, p, S_FP64, &p64))) return s;
+        PlanGuard pg64{p64};
+        DevBuf dW;
+        SF_CUDA(cudaMalloc(&dW.p, sizeof(double) * nnz + 16));
+        SyncOnExit sync64{st};
+        double* a = F;
+        double* bq = (double*)dW.p;
+        for (int r = 0; r < sq; ++r) {
+          if ((s = run_mul(p64->fwd, S_FP64, a, a, bq, st))) return s;
+          std::swap(a, bq);
+        }
+        if (a != F) SF_CUDA(cudaMemcpyAsync(F, a, sizeof(double) * nnz, cudaMemcpyDeviceToDevice, st));
+        SF_CUDA(cudaStreamSynchronize(st));
+      }
     }
     SF_CUDA(cudaStreamSynchronize(st));
     return S_OK;
   }
   return set_error(S_ERR_ARG, "s_funm: unknown function");
+}
+
+extern "C" s_status s_funm_sqrt_backward(s_pattern p, int steps, double c, const double* ck, const double* dF,
+                                         double* dA, void* stream) {
+  if (!p || !ck || !dF || !dA || steps < 1 || !(c > 0.0)) return set_error(S_ERR_ARG, "s_funm_sqrt_backward: bad argument");
+  if (!p->has_all_diag) return set_error(S_ERR_PATTERN, "s_funm_sqrt_backward: the pattern must hold every diagonal block");
+  cudaStream_t st = (cudaStream_t)stream;
+  const int64_t nnz = p->d.nnz;
+  s_plan plan = nullptr;
+  s_status s = s_plan_create(p, p, p, S_FP64, &plan);
+  if (s) return s;
+  struct PlanGuard {
+    s_plan q;
+    ~PlanGuard() { s_plan_destroy(q); }
+  } pg{plan};
+  const size_t bytes = sizeof(double) * nnz + 16;
+  DevBuf b[10];
+  for (auto& x : b) SF_CUDA(cudaMalloc(&x.p, bytes));
+  SyncOnExit sync{st};
+  double *dY = (double*)b[0].p, *dZ = (double*)b[1].p, *P = (double*)b[2].p, *T = (double*)b[3].p;
+  double *dYa = (double*)b[4].p, *dT1 = (double*)b[5].p, *dT2 = (double*)b[6].p, *dZa = (double*)b[7].p;
+  double *dZb = (double*)b[8].p, *dYb = (double*)b[9].p;
+  // X = sqrt(c) Y_steps:  dY_steps = sqrt(c) dF,  dZ_steps = 0
+  if ((s = run_add(p, S_FP64, std::sqrt(c), dF, 0.0, nullptr, 0.0, dY, st))) return s;
+  SF_CUDA(cudaMemsetAsync(dZ, 0, sizeof(double) * nnz, st));
+  for (int k = steps - 1; k >= 0; --k) {
+    const double* Y = ck + (int64_t)2 * k * nnz;
+    const double* Z = Y + nnz;
+    if ((s = run_mul(plan->fwd, S_FP64, Z, Y, P, st))) return s;                 // P = P_S(Z Y)
+    if ((s = run_add(p, S_FP64, -0.5, P, 0.0, nullptr, 1.5, T, st))) return s;   // T = (3I - P)/2
+    // Y' = P_S(Y T): dY_a = P_S(dY' T^T), dT_1 = P_S(Y^T dY')
+    if ((s = s_mul_masked_adjoint(plan, dY, Y, T, dYa, dT1, st))) return s;
+    // Z' = P_S(T Z): dT_2 = P_S(dZ' Z^T), dZ_a = P_S(T^T dZ')
+    if ((s = s_mul_masked_adjoint(plan, dZ, T, Z, dT2, dZa, st))) return s;
+    // T = (3I - P)/2: dP = -(dT_1 + dT_2)/2, kept in dT1
+    if ((s = run_add(p, S_FP64, -0.5, dT1, -0.5, dT2, 0.0, dT1, st))) return s;
+    // P = P_S(Z Y): dZ_b = P_S(dP Y^T), dY_b = P_S(Z^T dP)
+    if ((s = s_mul_masked_adjoint(plan, dT1, Z, Y, dZb, dYb, st))) return s;
+    if ((s = run_add(p, S_FP64, 1.0, dYa, 1.0, dYb, 0.0, dY, st))) return s;
+    if ((s = run_add(p, S_FP64, 1.0, dZa, 1.0, dZb, 0.0, dZ, st))) return s;
+  }
+  // Y_0 = A / c
+  if ((s = run_add(p, S_FP64, 1.0 / c, dY, 0.0, nullptr, 0.0, dA, st))) return s;
+  SF_CUDA(cudaStreamSynchronize(st));
+  return S_OK;
+}
+
+extern "C" s_status s_quad_form(s_pattern p, const double* X, const double* z, double* out, void* stream) {
+  if (!p || !X || !z || !out) return set_error(S_ERR_ARG, "s_quad_form: NULL argument");
+  cudaStream_t st = (cudaStream_t)stream;
+  const int64_t nb = p->d.nblocks;
+  DevBuf part, tot;
+  SF_CUDA(cudaMalloc(&part.p, sizeof(double) * (nb + 1)));
+  SF_CUDA(cudaMalloc(&tot.p, sizeof(double)));
+  SyncOnExit sync{st};
+  SF_CUDA(cudaMemsetAsync(tot.p, 0, sizeof(double), st));
+  if (nb) {
+    quad_part_kernel<<<(unsigned)((nb * 32 + 255) / 256), 256, 0, st>>>(nb, p->d.brow, p->d.colidx, p->d.bsize,
+                                                                      p->d.boff, p->d.voff, X, z, (double*)part.p);
+    // fixed-order sum of the block parts: dot with a vector of ones
+    DevBuf ones;
+    SF_CUDA(cudaMalloc(&ones.p, sizeof(double) * nb));
+    fill_kernel<<<grid_of(nb), 256, 0, st>>>(nb, 1.0, (double*)ones.p);
+    dot_kernel<<<1, 1024, 0, st>>>(nb, (const double*)part.p, (const double*)ones.p, (double*)tot.p);
+    SF_CUDA(cudaGetLastError());
+    SF_CUDA(cudaMemcpyAsync(out, tot.p, sizeof(double), cudaMemcpyDeviceToHost, st));
+    SF_CUDA(cudaStreamSynchronize(st));
+  } else {
+    *out = 0.0;
+  }
+  return S_OK;
+}
+
+extern "C" s_status s_quad_form_grad(s_pattern p, const double* z, double* dX, void* stream) {
+  if (!p || !z || (!dX && p->d.nnz > 0)) return set_error(S_ERR_ARG, "s_quad_form_grad: NULL argument");
+  const int64_t nb = p->d.nblocks;
+  if (nb)
+    quad_grad_kernel<<<(unsigned)((nb * 32 + 255) / 256), 256, 0, (cudaStream_t)stream>>>(
+        nb, p->d.brow, p->d.colidx, p->d.bsize, p->d.boff, p->d.voff, z, dX);
+  SF_CUDA(cudaGetLastError());
+  return S_OK;
 }

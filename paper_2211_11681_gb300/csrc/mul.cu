@@ -83,22 +83,21 @@ __global__ void count_kernel(DevSide x, DevSide y, const int32_t* bsize, const i
 
 // tiles per block
 __global__ void tile_count_kernel(const int32_t* bsize, const int32_t* c_brow, const int32_t* c_col, int64_t nblocks,
-                                  int32_t* ntile) {
+                                  int edge, int32_t* ntile) {
   int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (k >= nblocks) return;
   int ni = bsize[c_brow[k]], nj = bsize[c_col[k]];
-  ntile[k] = ((ni + kTile - 1) / kTile) * ((nj + kTile - 1) / kTile);
+  ntile[k] = ((ni + edge - 1) / edge) * ((nj + edge - 1) / edge);
 }
 
-__global__ void tile_fill_kernel(const int32_t* order, const int64_t* first, const int32_t* bsize,
-                                 const int32_t* c_brow, const int32_t* c_col, int64_t nblocks, Tile* tiles) {
-  int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (s >= nblocks) return;
-  int k = order[s];
+__global__ void tile_fill_kernel(const int64_t* first, const int32_t* bsize, const int32_t* c_brow,
+                                 const int32_t* c_col, int64_t nblocks, int edge, Tile* tiles) {
+  int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (k >= nblocks) return;
   int ni = bsize[c_brow[k]], nj = bsize[c_col[k]];
-  int64_t t = first[s];
-  for (int r0 = 0; r0 < ni; r0 += kTile)
-    for (int c0 = 0; c0 < nj; c0 += kTile) tiles[t++] = Tile{k, (int16_t)r0, (int16_t)c0};
+  int64_t t = first[k];
+  for (int r0 = 0; r0 < ni; r0 += edge)
+    for (int c0 = 0; c0 < nj; c0 += edge) tiles[t++] = Tile{(int32_t)k, (int16_t)r0, (int16_t)c0};
 }
 
 // ---- numeric kernels ----------------------------------------------------------------------
@@ -206,16 +205,17 @@ __global__ void __launch_bounds__(kWarps * 32) mul_kernel(MulArgs a, const T* __
 }
 
 // Float product: one warp per output tile as above, with register micro-tiles and
-// double-buffered asynchronous staging.  Lane (mr, mc) of the first 25 lanes owns rows
-// 4mr..4mr+3 and columns 4mc..4mc+3 of the tile.  The warp first lists the matching
-// lambda blocks of a batch (a "stage" per kTile-wide slice of a lambda block), then streams
-// them: while stage s is multiplied out of shared memory, the copies of stage s+1 are in
-// flight (cp.async, 4-byte copies scatter op(X) transposed into sA[t][r], op(Y) lands in
-// sB[t][c]).  Each t step is one float4 load of each buffer and 16 FMAs.  Products are
-// summed in a float partial that is folded into the accumulator with an error-free
-// two-sum every kFold lambda blocks (compensated summation over lambda).
+// double-buffered asynchronous staging.  Template parameters: tile edge TT and the
+// micro-tile MR x MC of a lane; lane (mr, mc) of the first (TT/MR)(TT/MC) lanes owns rows
+// MR*mr .. MR*mr+MR-1 and columns MC*mc .. MC*mc+MC-1 of the tile.  The warp first lists
+// the matching lambda blocks of a batch, then streams them slice by slice (a slice = TT
+// values of lambda): while one slice is multiplied out of shared memory, the copies of the
+// next are in flight (cp.async; 4-byte copies scatter op(X) transposed into sA[t][r],
+// op(Y) lands in sB[t][c], 16-byte copies where rows are contiguous and aligned).  Each t
+// step loads MR values of sA and MC values of sB and does MR*MC FMAs.  Products are summed
+// in a float partial that is folded into the accumulator with an error-free two-sum every
+// kFold lambda blocks (compensated summation over lambda).
 constexpr int kF32Warps = 4;
-constexpr int kLd = kTile;       // 20: row length of sA / sB; float4 slots at 4*m are 16-byte aligned
 constexpr int kStages = 64;      // matching lambda blocks listed per batch
 constexpr int kFold = 4;         // lambda blocks per two-sum
 
@@ -238,19 +238,34 @@ __device__ __forceinline__ void cp_wait() {
   asm volatile("cp.async.wait_group %0;\n" ::"n"(N));
 }
 
-template <bool TX, bool TY>
+// M consecutive floats from shared memory (aligned to M floats when M is 2 or 4)
+template <int M>
+__device__ __forceinline__ void lds(const float* p, float* out) {
+  if constexpr (M == 4) {
+    const float4 v = *reinterpret_cast<const float4*>(p);
+    out[0] = v.x, out[1] = v.y, out[2] = v.z, out[3] = v.w;
+  } else if constexpr (M == 2) {
+    const float2 v = *reinterpret_cast<const float2*>(p);
+    out[0] = v.x, out[1] = v.y;
+  } else {
+#pragma unroll
+    for (int q = 0; q < M; ++q) out[q] = p[q];
+  }
+}
+
+template <int TT, bool TX, bool TY>
 __device__ __forceinline__ void stage_copy(const Stage& sg, const float* __restrict__ X, const float* __restrict__ Y,
                                            const int64_t* xvoff, const int64_t* yvoff, int ni, int nj, int r0,
                                            int c0, int th, int tw, int lane, float* xs, float* ys) {
   const int nl = sg.nl, t0 = sg.t0;
-  const int tk = min(kTile, nl - t0);
+  const int tk = min(TT, nl - t0);
   const float* xb = X + xvoff[sg.bx];
   const float* yb = Y + yvoff[sg.by];
   const float rtk = 1.0f / (float)tk;
   for (int e = lane; e < th * tk; e += 32) {
     const int r = __float2int_rz(((float)e + 0.5f) * rtk), tt = e - r * tk;
     const int gr = r0 + r, gt = t0 + tt;
-    cp_async4(xs + tt * kLd + r, TX ? xb + (int64_t)gt * ni + gr : xb + (int64_t)gr * nl + gt);
+    cp_async4(xs + tt * TT + r, TX ? xb + (int64_t)gt * ni + gr : xb + (int64_t)gr * nl + gt);
   }
   const bool vec = !TY && c0 == 0 && tw == nj && (nj & 3) == 0 && ((reinterpret_cast<uintptr_t>(yb) & 15) == 0);
   if (vec) {
@@ -258,31 +273,33 @@ __device__ __forceinline__ void stage_copy(const Stage& sg, const float* __restr
     for (int q = lane; q < (tk * nj) >> 2; q += 32) {
       const int e = q << 2;
       const int tt = __float2int_rz(((float)e + 0.5f) * rnj), c = e - tt * nj;
-      cp_async16(ys + tt * kLd + c, yb + (int64_t)(t0 + tt) * nj + c);
+      cp_async16(ys + tt * TT + c, yb + (int64_t)(t0 + tt) * nj + c);
     }
   } else {
     const float rtw = 1.0f / (float)tw;
     for (int e = lane; e < tk * tw; e += 32) {
       const int tt = __float2int_rz(((float)e + 0.5f) * rtw), c = e - tt * tw;
       const int gt = t0 + tt, gc = c0 + c;
-      cp_async4(ys + tt * kLd + c, TY ? yb + (int64_t)gc * nl + gt : yb + (int64_t)gt * nj + gc);
+      cp_async4(ys + tt * TT + c, TY ? yb + (int64_t)gc * nl + gt : yb + (int64_t)gt * nj + gc);
     }
   }
 }
 
-template <bool TX, bool TY>
+template <int TT, int MR, int MC, bool TX, bool TY>
 __global__ void __launch_bounds__(kF32Warps * 32, 4) mul_f32_kernel(MulArgs a, const float* __restrict__ X,
                                                                     const float* __restrict__ Y,
                                                                     float* __restrict__ C) {
-  __shared__ __align__(16) float sA[kF32Warps][2][kTile * kLd];
-  __shared__ __align__(16) float sB[kF32Warps][2][kTile * kLd];
+  constexpr int GR = TT / MR, GC = TT / MC, NA = GR * GC, NQ = MR * MC;
+  static_assert(TT % MR == 0 && TT % MC == 0 && NA <= 32 && TT % 4 == 0, "bad micro-tile");
+  __shared__ __align__(16) float sA[kF32Warps][2][TT * TT];
+  __shared__ __align__(16) float sB[kF32Warps][2][TT * TT];
   __shared__ Stage sStage[kF32Warps][kStages];  // the batch's matching lambda blocks
   const int lane = threadIdx.x & 31;
   const int w = threadIdx.x >> 5;
   Stage* st = sStage[w];
-  const bool active = lane < 25;
-  const int mr = active ? lane / 5 : 0, mc = active ? lane % 5 : 0;
-  const int rl = 4 * mr, cl = 4 * mc;
+  const bool active = lane < NA;
+  const int mr = active ? lane / GC : 0, mc = active ? lane % GC : 0;
+  const int rl = MR * mr, cl = MC * mc;
   for (;;) {
     unsigned int t = 0;
     if (lane == 0) t = atomicAdd(a.counter, 1u);
@@ -292,10 +309,10 @@ __global__ void __launch_bounds__(kF32Warps * 32, 4) mul_f32_kernel(MulArgs a, c
     const int k = tile.blk;
     const int nu = a.c_brow[k], nup = a.c_col[k];
     const int ni = a.bsize[nu], nj = a.bsize[nup];
-    const int th = min(kTile, ni - tile.r0), tw = min(kTile, nj - tile.c0);
-    float acc[16], comp[16], p[16];
+    const int th = min(TT, ni - tile.r0), tw = min(TT, nj - tile.c0);
+    float acc[NQ], comp[NQ], p[NQ];
 #pragma unroll
-    for (int q = 0; q < 16; ++q) acc[q] = comp[q] = p[q] = 0.0f;
+    for (int q = 0; q < NQ; ++q) acc[q] = comp[q] = p[q] = 0.0f;
     int folded = 0;  // lambda blocks summed into p since the last two-sum
     const int px1 = (int)a.x.ptr[nu + 1];
     int px = (int)a.x.ptr[nu];
@@ -322,52 +339,49 @@ __global__ void __launch_bounds__(kF32Warps * 32, 4) mul_f32_kernel(MulArgs a, c
       }
       __syncwarp();
       if (nm == 0) continue;
-      // ---- stream the stages (lambda block m, slice q): copies of the next stage overlap
+      // ---- stream the slices (lambda block m, slice q): copies of the next slice overlap
       // the FMAs of the current one
-      int m = 0, q = 0;   // current stage
-      {
-        Stage sg = st[0];
-        stage_copy<TX, TY>(sg, X, Y, a.x.voff, a.y.voff, ni, nj, tile.r0, tile.c0, th, tw, lane, sA[w][0], sB[w][0]);
-        cp_commit();
-      }
+      int m = 0, q = 0;
+      stage_copy<TT, TX, TY>(st[0], X, Y, a.x.voff, a.y.voff, ni, nj, tile.r0, tile.c0, th, tw, lane, sA[w][0],
+                             sB[w][0]);
+      cp_commit();
       int buf = 0;
       for (;;) {
         const Stage cur = st[m];
-        const int t0 = q * kTile;
-        const bool last_slice = t0 + kTile >= (int)cur.nl;
+        const int t0 = q * TT;
+        const bool last_slice = t0 + TT >= (int)cur.nl;
         const int nm2 = last_slice ? m + 1 : m, nq2 = last_slice ? 0 : q + 1;
         const bool more = nm2 < nm;
         if (more) {
           Stage sg = st[nm2];
-          sg.t0 = (int16_t)(nq2 * kTile);
-          stage_copy<TX, TY>(sg, X, Y, a.x.voff, a.y.voff, ni, nj, tile.r0, tile.c0, th, tw, lane, sA[w][buf ^ 1],
-                             sB[w][buf ^ 1]);
+          sg.t0 = (int16_t)(nq2 * TT);
+          stage_copy<TT, TX, TY>(sg, X, Y, a.x.voff, a.y.voff, ni, nj, tile.r0, tile.c0, th, tw, lane,
+                                 sA[w][buf ^ 1], sB[w][buf ^ 1]);
           cp_commit();
           cp_wait<1>();
         } else {
           cp_wait<0>();
         }
         __syncwarp();
-        const int tk = min(kTile, (int)cur.nl - t0);
+        const int tk = min(TT, (int)cur.nl - t0);
         if (active) {
           const float* xs = sA[w][buf];
           const float* ys = sB[w][buf];
           for (int tt = 0; tt < tk; ++tt) {
-            const float4 av = *reinterpret_cast<const float4*>(xs + tt * kLd + rl);
-            const float4 bv = *reinterpret_cast<const float4*>(ys + tt * kLd + cl);
-            const float ar[4] = {av.x, av.y, av.z, av.w};
-            const float br[4] = {bv.x, bv.y, bv.z, bv.w};
+            float ar[MR], br[MC];
+            lds<MR>(xs + tt * TT + rl, ar);
+            lds<MC>(ys + tt * TT + cl, br);
 #pragma unroll
-            for (int ii = 0; ii < 4; ++ii)
+            for (int ii = 0; ii < MR; ++ii)
 #pragma unroll
-              for (int jj = 0; jj < 4; ++jj) p[ii * 4 + jj] = fmaf(ar[ii], br[jj], p[ii * 4 + jj]);
+              for (int jj = 0; jj < MC; ++jj) p[ii * MC + jj] = fmaf(ar[ii], br[jj], p[ii * MC + jj]);
           }
         }
         __syncwarp();
         if (last_slice && ++folded == kFold) {
           folded = 0;
 #pragma unroll
-          for (int qq = 0; qq < 16; ++qq) {
+          for (int qq = 0; qq < NQ; ++qq) {
             const float hi = acc[qq] + p[qq];
             const float bp = hi - acc[qq];
             comp[qq] += (acc[qq] - (hi - bp)) + (p[qq] - bp);
@@ -384,19 +398,26 @@ __global__ void __launch_bounds__(kF32Warps * 32, 4) mul_f32_kernel(MulArgs a, c
     if (active) {
       float* cb = C + a.c_voff[k];
 #pragma unroll
-      for (int ii = 0; ii < 4; ++ii)
+      for (int ii = 0; ii < MR; ++ii)
 #pragma unroll
-        for (int jj = 0; jj < 4; ++jj) {
-          const int q = ii * 4 + jj;
-          const float hi = acc[q] + p[q];
-          const float bp = hi - acc[q];
-          const float err = (acc[q] - (hi - bp)) + (p[q] - bp);
+        for (int jj = 0; jj < MC; ++jj) {
+          const int qq = ii * MC + jj;
+          const float hi = acc[qq] + p[qq];
+          const float bp = hi - acc[qq];
+          const float err = (acc[qq] - (hi - bp)) + (p[qq] - bp);
           const int r = rl + ii, c = cl + jj;
-          if (r < th && c < tw) cb[(int64_t)(tile.r0 + r) * nj + tile.c0 + c] = hi + (comp[q] + err);
+          if (r < th && c < tw) cb[(int64_t)(tile.r0 + r) * nj + tile.c0 + c] = hi + (comp[qq] + err);
         }
     }
   }
 }
+
+// The float kernel variants the autotuner chooses from: tile edge and lane micro-tile.
+struct F32Variant {
+  int tt, mr, mc;
+};
+constexpr F32Variant kF32Variants[] = {{20, 4, 4}, {16, 4, 2}, {12, 3, 2}, {8, 2, 1}};
+constexpr int kNumF32Variants = 4;
 
 static int g_sms = 0;
 static int num_sms() {
@@ -417,6 +438,49 @@ static Side side_of(const s_pattern_t* p, bool row_side, bool trans) {
   return Side{d.colptr, d.rowidx, d.cscblk, d.voff, trans};
 }
 
+// Tile list of S_C for tile edge `edge`, in block order: breadth-first block rows are
+// spatially coherent, so warps that run at the same time share lambda blocks in L2, and
+// the coarse (heavy) rows come first.
+s_status build_tiles(MulDesc* d, int edge) {
+  const s_pattern_t* C = d->pc;
+  const int64_t nb = C->d.nblocks;
+  cudaFree(d->tiles);
+  d->tiles = nullptr;
+  d->ntiles = 0;
+  d->edge = edge;
+  if (nb == 0) {
+    SF_CUDA(cudaMalloc(&d->tiles, sizeof(Tile)));
+    return S_OK;
+  }
+  int32_t* ntile = nullptr;
+  int64_t* first = nullptr;
+  cudaError_t e = cudaMalloc(&ntile, sizeof(int32_t) * nb);
+  if (e == cudaSuccess) e = cudaMalloc(&first, sizeof(int64_t) * (nb + 1));
+  if (e == cudaSuccess) {
+    const int g = (int)((nb + 255) / 256);
+    tile_count_kernel<<<g, 256>>>(C->d.bsize, C->d.brow, C->d.colidx, nb, edge, ntile);
+    e = cudaGetLastError();
+    std::vector<int32_t> nt(nb);
+    std::vector<int64_t> fst(nb + 1, 0);
+    if (e == cudaSuccess) e = cudaMemcpy(nt.data(), ntile, sizeof(int32_t) * nb, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) {
+      for (int64_t k = 0; k < nb; ++k) fst[k + 1] = fst[k] + nt[k];
+      d->ntiles = fst[nb];
+      e = cudaMemcpy(first, fst.data(), sizeof(int64_t) * (nb + 1), cudaMemcpyHostToDevice);
+    }
+    if (e == cudaSuccess) e = cudaMalloc(&d->tiles, sizeof(Tile) * std::max<int64_t>(d->ntiles, 1));
+    if (e == cudaSuccess) {
+      tile_fill_kernel<<<g, 256>>>(first, C->d.bsize, C->d.brow, C->d.colidx, nb, edge, d->tiles);
+      e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  }
+  cudaFree(ntile);
+  cudaFree(first);
+  if (e != cudaSuccess) return cuda_error(e, "build_tiles");
+  return S_OK;
+}
+
 s_status build_desc(const s_pattern_t* X, bool tx, const s_pattern_t* Y, bool ty, const s_pattern_t* C, s_prec prec,
                     MulDesc* out) {
   (void)prec;
@@ -429,77 +493,33 @@ s_status build_desc(const s_pattern_t* X, bool tx, const s_pattern_t* Y, bool ty
   const int64_t nb = C->d.nblocks;
   unsigned long long* dtrip = nullptr;
   double* bflops = nullptr;
-  int32_t* ntile = nullptr;
-  int32_t* order = nullptr;
-  int64_t* first = nullptr;
   s_status st = S_OK;
-  cudaError_t e;
-#define TRY(call)                         \
-  do {                                    \
-    e = (call);                           \
-    if (e != cudaSuccess) {               \
-      st = cuda_error(e, #call);          \
-      goto done;                          \
-    }                                     \
-  } while (0)
-  TRY(cudaMalloc(&dtrip, sizeof(unsigned long long)));
-  TRY(cudaMemset(dtrip, 0, sizeof(unsigned long long)));
-  TRY(cudaMalloc(&bflops, sizeof(double) * std::max<int64_t>(nb, 1)));
-  TRY(cudaMalloc(&ntile, sizeof(int32_t) * std::max<int64_t>(nb, 1)));
-  TRY(cudaMalloc(&order, sizeof(int32_t) * std::max<int64_t>(nb, 1)));
-  TRY(cudaMalloc(&first, sizeof(int64_t) * (nb + 1)));
-  TRY(cudaMalloc(&d.counter, sizeof(unsigned int)));
-  if (nb > 0) {
-    int threads = 256;
-    int blocks = (int)std::min<int64_t>((nb * 32 + threads - 1) / threads, (int64_t)num_sms() * 16);
+  cudaError_t e = cudaMalloc(&dtrip, sizeof(unsigned long long));
+  if (e == cudaSuccess) e = cudaMemset(dtrip, 0, sizeof(unsigned long long));
+  if (e == cudaSuccess) e = cudaMalloc(&bflops, sizeof(double) * std::max<int64_t>(nb, 1));
+  if (e == cudaSuccess) e = cudaMalloc(&d.counter, sizeof(unsigned int));
+  if (e == cudaSuccess && nb > 0) {
+    const int threads = 256;
+    const int blocks = (int)std::min<int64_t>((nb * 32 + threads - 1) / threads, (int64_t)num_sms() * 16);
     count_kernel<<<blocks, threads>>>(dev_side(d.x), dev_side(d.y), C->d.bsize, C->d.brow, C->d.colidx, nb, dtrip,
                                       bflops);
-    TRY(cudaGetLastError());
-    int g = (int)((nb + 255) / 256);
-    tile_count_kernel<<<g, 256>>>(C->d.bsize, C->d.brow, C->d.colidx, nb, ntile);
-    TRY(cudaGetLastError());
-    // tiles in block order: breadth-first block rows are spatially coherent, so warps that
-    // run at the same time share lambda blocks in L2; coarse (heavy) rows come first
-    {
-      std::vector<int32_t> iota(nb);
-      for (int64_t k = 0; k < nb; ++k) iota[k] = (int32_t)k;
-      TRY(cudaMemcpy(order, iota.data(), sizeof(int32_t) * nb, cudaMemcpyHostToDevice));
-    }
-    // tiles per block in sorted order, exclusive scan -> first tile of each sorted block
-    {
-      std::vector<int32_t> nt(nb), ord(nb);
-      TRY(cudaMemcpy(nt.data(), ntile, sizeof(int32_t) * nb, cudaMemcpyDeviceToHost));
-      TRY(cudaMemcpy(ord.data(), order, sizeof(int32_t) * nb, cudaMemcpyDeviceToHost));
-      std::vector<int64_t> fst(nb + 1);
-      fst[0] = 0;
-      for (int64_t s = 0; s < nb; ++s) fst[s + 1] = fst[s] + nt[ord[s]];
-      d.ntiles = fst[nb];
-      TRY(cudaMemcpy(first, fst.data(), sizeof(int64_t) * (nb + 1), cudaMemcpyHostToDevice));
-    }
-    TRY(cudaMalloc(&d.tiles, sizeof(Tile) * std::max<int64_t>(d.ntiles, 1)));
-    tile_fill_kernel<<<g, 256>>>(order, first, C->d.bsize, C->d.brow, C->d.colidx, nb, d.tiles);
-    TRY(cudaGetLastError());
-    {
-      unsigned long long tr = 0;
-      TRY(cudaMemcpy(&tr, dtrip, sizeof(tr), cudaMemcpyDeviceToHost));
+    e = cudaGetLastError();
+    unsigned long long tr = 0;
+    if (e == cudaSuccess) e = cudaMemcpy(&tr, dtrip, sizeof(tr), cudaMemcpyDeviceToHost);
+    std::vector<double> bf(nb);
+    if (e == cudaSuccess) e = cudaMemcpy(bf.data(), bflops, sizeof(double) * nb, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) {
       d.triples = (int64_t)tr;
-      std::vector<double> bf(nb);
-      TRY(cudaMemcpy(bf.data(), bflops, sizeof(double) * nb, cudaMemcpyDeviceToHost));
       double f = 0.0;
       for (double v : bf) f += v;
       d.flops = f;
     }
-  } else {
-    TRY(cudaMalloc(&d.tiles, sizeof(Tile)));
   }
-done:
-#undef TRY
   cudaFree(dtrip);
   cudaFree(bflops);
-  cudaFree(ntile);
-  cudaFree(order);
-  cudaFree(first);
-  if (st != S_OK) {
+  if (e != cudaSuccess) st = cuda_error(e, "s_plan_create(symbolic)");
+  if (!st) st = build_tiles(&d, kF32Variants[0].tt);
+  if (st) {
     free_desc(&d);
     return st;
   }
@@ -513,6 +533,24 @@ void free_desc(MulDesc* d) {
   d->tiles = nullptr;
   d->counter = nullptr;
   d->ntiles = 0;
+}
+
+using F32Kernel = void (*)(MulArgs, const float*, const float*, float*);
+
+template <int V>
+static F32Kernel f32_kernel(bool tx, bool ty) {
+  constexpr int TT = kF32Variants[V].tt, MR = kF32Variants[V].mr, MC = kF32Variants[V].mc;
+  return tx ? (ty ? mul_f32_kernel<TT, MR, MC, true, true> : mul_f32_kernel<TT, MR, MC, true, false>)
+            : (ty ? mul_f32_kernel<TT, MR, MC, false, true> : mul_f32_kernel<TT, MR, MC, false, false>);
+}
+
+static F32Kernel f32_kernel_of(int v, bool tx, bool ty) {
+  switch (v) {
+    case 1: return f32_kernel<1>(tx, ty);
+    case 2: return f32_kernel<2>(tx, ty);
+    case 3: return f32_kernel<3>(tx, ty);
+    default: return f32_kernel<0>(tx, ty);
+  }
 }
 
 template <typename T>
@@ -534,10 +572,11 @@ static s_status launch_typed(const MulDesc& d, const void* X, const void* Y, voi
   K kern;
   int warps;
   if constexpr (sizeof(T) == 4) {
-    kern = d.x.trans ? (d.y.trans ? mul_f32_kernel<true, true> : mul_f32_kernel<true, false>)
-                     : (d.y.trans ? mul_f32_kernel<false, true> : mul_f32_kernel<false, false>);
+    if (d.edge != kF32Variants[d.variant].tt) return set_error(S_ERR_ARG, "internal: tile list does not match variant");
+    kern = f32_kernel_of(d.variant, d.x.trans, d.y.trans);
     warps = kF32Warps;
   } else {
+    if (d.edge != kTile) return set_error(S_ERR_ARG, "internal: double kernel needs 20-wide tiles");
     kern = d.x.trans ? (d.y.trans ? mul_kernel<T, true, true> : mul_kernel<T, true, false>)
                      : (d.y.trans ? mul_kernel<T, false, true> : mul_kernel<T, false, false>);
     warps = kWarps;
@@ -642,3 +681,67 @@ extern "C" s_status s_mul_masked_adjoint(s_plan p, const void* dC, const void* A
   }
   return S_OK;
 }
+
+extern "C" s_status s_plan_autotune(s_plan p, const void* A, const void* B, void* C, void* stream, int* chosen) {
+  if (!p || !A || !B || !C) return set_error(S_ERR_ARG, "s_plan_autotune: NULL argument");
+  if (p->prec != S_FP32) {
+    if (chosen) *chosen = 0;
+    return S_OK;  // one kernel shape for the double path
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaEvent_t e0, e1;
+  SF_CUDA(cudaEventCreate(&e0));
+  SF_CUDA(cudaEventCreate(&e1));
+  float best = 1e30f;
+  int bestv = 0;
+  s_status s = S_OK;
+  for (int v = 0; v < kNumF32Variants && !s; ++v) {
+    if ((s = build_tiles(&p->fwd, kF32Variants[v].tt))) break;
+    p->fwd.variant = v;
+    if ((s = run_mul(p->fwd, S_FP32, A, B, C, st))) break;  // warm-up
+    cudaEventRecord(e0, st);
+    for (int r = 0; r < 3 && !s; ++r) s = run_mul(p->fwd, S_FP32, A, B, C, st);
+    cudaEventRecord(e1, st);
+    cudaError_t e = cudaEventSynchronize(e1);
+    if (e != cudaSuccess) {
+      s = cuda_error(e, "s_plan_autotune");
+      break;
+    }
+    float ms = 0.0f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    p->tune_ms[v] = ms / 3.0f;
+    if (ms < best) {
+      best = ms;
+      bestv = v;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (s) return s;
+  if ((s = build_tiles(&p->fwd, kF32Variants[bestv].tt))) return s;
+  p->fwd.variant = bestv;
+  if (chosen) *chosen = bestv;
+  return S_OK;
+}
+
+extern "C" s_status s_plan_variant(s_plan p, int variant, int* tile, int* micro_rows, int* micro_cols) {
+  if (!p) return set_error(S_ERR_ARG, "s_plan_variant: NULL plan");
+  if (variant < 0) variant = p->fwd.variant;
+  if (variant >= kNumF32Variants) return set_error(S_ERR_ARG, "s_plan_variant: no such variant");
+  if (tile) *tile = kF32Variants[variant].tt;
+  if (micro_rows) *micro_rows = kF32Variants[variant].mr;
+  if (micro_cols) *micro_cols = kF32Variants[variant].mc;
+  return S_OK;
+}
+
+extern "C" s_status s_plan_set_variant(s_plan p, int variant) {
+  if (!p) return set_error(S_ERR_ARG, "s_plan_set_variant: NULL plan");
+  if (variant < 0 || variant >= kNumF32Variants) return set_error(S_ERR_ARG, "s_plan_set_variant: no such variant");
+  if (p->prec != S_FP32) return set_error(S_ERR_ARG, "s_plan_set_variant: only float plans have variants");
+  s_status s = build_tiles(&p->fwd, kF32Variants[variant].tt);
+  if (s) return s;
+  p->fwd.variant = variant;
+  return S_OK;
+}
+
+extern "C" int s_plan_num_variants(void) { return kNumF32Variants; }

@@ -170,3 +170,26 @@ extern "C" s_status s_pattern_host_arrays(s_pattern p, int32_t* n_clusters, cons
   if (colidx) *colidx = p->colidx.data();
   return S_OK;
 }
+
+extern "C" s_status s_pattern_concat(int32_t count, const s_pattern* parts, s_pattern* out) {
+  if (!out) return set_error(S_ERR_ARG, "s_pattern_concat: out is NULL");
+  *out = nullptr;
+  if (count < 1 || !parts) return set_error(S_ERR_ARG, "s_pattern_concat: no parts");
+  std::vector<int64_t> bo{0}, rp{0};
+  std::vector<int32_t> lv, ci;
+  int64_t nc_total = 0;
+  for (int32_t q = 0; q < count; ++q) {
+    const s_pattern_t* p = parts[q];
+    if (!p) return set_error(S_ERR_ARG, "s_pattern_concat: NULL part");
+    if (nc_total + p->d.nc > INT32_MAX) return set_error(S_ERR_ARG, "s_pattern_concat: too many clusters");
+    const int64_t row0 = bo.back(), blk0 = rp.back();
+    for (int32_t i = 0; i < p->d.nc; ++i) {
+      bo.push_back(row0 + p->boff[i + 1]);
+      rp.push_back(blk0 + p->rowptr[i + 1]);
+      lv.push_back(p->level[i]);
+    }
+    for (int32_t c : p->colidx) ci.push_back((int32_t)(c + nc_total));
+    nc_total += p->d.nc;
+  }
+  return s_pattern_create((int32_t)nc_total, bo.data(), lv.data(), rp.data(), ci.data(), out);
+}

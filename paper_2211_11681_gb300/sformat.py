@@ -43,12 +43,23 @@ def _load():
         "s_plan_create": (i32, [vp, vp, vp, i32, P(vp)]),
         "s_plan_destroy": (i32, [vp]),
         "s_plan_stats": (i32, [vp, P(i64), P(dbl)]),
+        "s_plan_autotune": (i32, [vp, vp, vp, vp, vp, P(i32)]),
+        "s_plan_variant": (i32, [vp, i32, P(i32), P(i32), P(i32)]),
+        "s_plan_set_variant": (i32, [vp, i32]),
+        "s_plan_num_variants": (i32, []),
+        "s_pattern_concat": (i32, [i32, P(vp), P(vp)]),
+        "s_graph_capture_mul": (i32, [vp, vp, vp, vp, P(vp)]),
+        "s_graph_launch": (i32, [vp, vp]),
+        "s_graph_destroy": (i32, [vp]),
         "s_mul_masked": (i32, [vp, vp, vp, vp, vp]),
         "s_mul_masked_adjoint": (i32, [vp, vp, vp, vp, vp, vp, vp]),
         "s_add": (i32, [vp, i32, dbl, vp, dbl, vp, dbl, vp, vp]),
         "s_norm_est": (i32, [vp, vp, i32, P(dbl), vp]),
         "s_norm_est_noalloc": (i32, [vp, vp, i32, P(dbl), vp]),
         "s_funm": (i32, [vp, i32, vp, vp, vp, vp]),
+        "s_funm_sqrt_backward": (i32, [vp, i32, dbl, vp, vp, vp, vp]),
+        "s_quad_form": (i32, [vp, vp, vp, P(dbl), vp]),
+        "s_quad_form_grad": (i32, [vp, vp, vp, vp]),
         "s_last_error": (ctypes.c_char_p, []),
         "s_version": (ctypes.c_char_p, []),
     }
@@ -65,7 +76,8 @@ lib = _load()
 class FunmOpts(ctypes.Structure):
     _fields_ = [("steps", ctypes.c_int), ("taylor_degree", ctypes.c_int), ("prec", ctypes.c_int),
                 ("scale", ctypes.c_double), ("squarings", ctypes.c_int),
-                ("residual", ctypes.POINTER(ctypes.c_double)), ("checkpoints", ctypes.c_void_p)]
+                ("residual", ctypes.POINTER(ctypes.c_double)), ("checkpoints", ctypes.c_void_p),
+                ("refine", ctypes.c_int)]
 
 
 def check(st):
@@ -164,6 +176,26 @@ class Plan:
         check(lib.s_plan_stats(self.h, ctypes.byref(t), ctypes.byref(f)))
         return int(t.value), float(f.value)
 
+    def autotune(self, A, B, C, stream=None):
+        """Pick the fastest float kernel variant on these operands; returns its shape."""
+        v = ctypes.c_int32(-1)
+        check(lib.s_plan_autotune(self.h, _ptr(A), _ptr(B), _ptr(C), _stream(stream), ctypes.byref(v)))
+        self.variant_index = v.value
+        return self.variant()
+
+    def set_variant(self, v):
+        check(lib.s_plan_set_variant(self.h, int(v)))
+        self.variant_index = int(v)
+
+    def variant(self):
+        t, r, c = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+        check(lib.s_plan_variant(self.h, -1, ctypes.byref(t), ctypes.byref(r), ctypes.byref(c)))
+        return {"tile": t.value, "micro": (r.value, c.value)}
+
+    def graph(self, A, B, C):
+        """CUDA graph of mul(A, B, C) on these buffers."""
+        return Graph(self, A, B, C)
+
     def mul(self, A, B, C, stream=None):
         check(lib.s_mul_masked(self.h, _ptr(A), _ptr(B), _ptr(C), _stream(stream)))
         return C
@@ -182,6 +214,52 @@ class Plan:
             self.close()
         except Exception:
             pass
+
+
+class Graph:
+    def __init__(self, plan, A, B, C):
+        self.keep = (plan, A, B, C)
+        h = ctypes.c_void_p()
+        check(lib.s_graph_capture_mul(plan.h, _ptr(A), _ptr(B), _ptr(C), ctypes.byref(h)))
+        self.h = h
+
+    def launch(self, stream=None):
+        check(lib.s_graph_launch(self.h, _stream(stream)))
+
+    def __del__(self):
+        try:
+            if self.h.value:
+                lib.s_graph_destroy(self.h)
+        except Exception:
+            pass
+
+
+class _Owned:
+    """A pattern handle created by the library (s_pattern_concat)."""
+
+    def __init__(self, h):
+        self.h = h
+
+    nnz = property(lambda self: int(lib.s_pattern_nnz(self.h)))
+    nblocks = property(lambda self: int(lib.s_pattern_nblocks(self.h)))
+
+    def arrays(self):
+        return pattern_arrays(self.h)
+
+    def __del__(self):
+        try:
+            if self.h.value:
+                lib.s_pattern_destroy(self.h)
+        except Exception:
+            pass
+
+
+def concat(patterns):
+    """One pattern holding the given patterns' matrices side by side (s_pattern_concat)."""
+    arr = (ctypes.c_void_p * len(patterns))(*[p.h.value for p in patterns])
+    h = ctypes.c_void_p()
+    check(lib.s_pattern_concat(len(patterns), arr, ctypes.byref(h)))
+    return _Owned(h)
 
 
 def add(pattern, A, B, C, alpha=1.0, beta=1.0, gamma=0.0, prec="fp64", stream=None):
@@ -205,16 +283,33 @@ def norm_est_noalloc(pattern, A, iters=50, stream=None):
 
 
 def funm(pattern, fn, A, F, steps=0, taylor_degree=0, prec="fp64", scale=0.0, squarings=-1, residual=False,
-         checkpoints=None, stream=None):
+         checkpoints=None, refine=0, stream=None):
     """F = f(A) with f in {"sqrt", "exp", "exp_neg"}; returns the residual for sqrt if asked."""
     code = {"sqrt": S_SQRT, "exp": S_EXP, "exp_neg": S_EXP_NEG}[fn]
     res = ctypes.c_double(-1.0)
     o = FunmOpts(int(steps), int(taylor_degree), PREC[prec] if isinstance(prec, str) else int(prec),
                  float(scale), int(squarings), ctypes.pointer(res) if residual else None,
-                 _ptr(checkpoints))
+                 _ptr(checkpoints), int(refine))
     check(lib.s_funm(pattern.h, code, _ptr(A), _ptr(F), ctypes.byref(o), _stream(stream)))
     return float(res.value) if residual else None
 
 
 def version():
     return lib.s_version().decode()
+
+
+def sqrt_backward(pattern, steps, c, checkpoints, dF, dA, stream=None):
+    check(lib.s_funm_sqrt_backward(pattern.h, int(steps), float(c), _ptr(checkpoints), _ptr(dF), _ptr(dA),
+                                   _stream(stream)))
+    return dA
+
+
+def quad_form(pattern, X, z, stream=None):
+    out = ctypes.c_double()
+    check(lib.s_quad_form(pattern.h, _ptr(X), _ptr(z), ctypes.byref(out), _stream(stream)))
+    return float(out.value)
+
+
+def quad_form_grad(pattern, z, dX, stream=None):
+    check(lib.s_quad_form_grad(pattern.h, _ptr(z), _ptr(dX), _stream(stream)))
+    return dX

@@ -53,3 +53,40 @@ def test_exp_parity(sphere, fn, sign):
         sf.funm(P, fn, dev(As.val), F)
         E = ofunm.expm_taylor(As, sign=sign, nthreads=8)
         assert rel_frob(host(F), E.val) <= 1e-10
+
+
+def test_mixed_sqrt_with_double_residual_correction(sphere):
+    # float Newton-Schulz steps, then two residual-correction steps in double
+    # (R = A/c - P_S(Y Y), Y += P_S(Z R)/2): the coupled iteration keeps Y Z^{-1} = A/c, so
+    # its own steps never remove the float error in that direction; the correction does.
+    # The oracle runs the same method in double throughout.  The correction contracts
+    # linearly (Z is only an approximate inverse on the pattern; factors ~0.1 and ~0.25 per
+    # step on this matrix in the oracle), so a float start 1.8e-7 away ends ~1e-8 from the
+    # double-started result after two steps: bound 3e-8.
+    from paper_2211_11681_gb300 import sformat as sf
+    c, levels = sphere
+    A = c.A
+    P = pattern_of(A, levels)
+    X = ofunm.sqrtm_ns(A, steps=25, nthreads=8, refine=2)
+    F = dev(np.zeros(len(A.val)))
+    res = sf.funm(P, "sqrt", dev(A.val), F, steps=25, prec="fp32", refine=2, residual=True)
+    assert rel_frob(host(F), X.val) <= 3e-8
+    F64 = dev(np.zeros(len(A.val)))
+    res64 = sf.funm(P, "sqrt", dev(A.val), F64, steps=25, refine=2, residual=True)
+    assert rel_frob(host(F64), X.val) <= 1e-10
+    assert res64 == pytest.approx(ofunm.sqrt_residual(X, A, nthreads=8), rel=1e-4)
+    # the corrected float result keeps the residual of double Newton-Schulz
+    F0 = dev(np.zeros(len(A.val)))
+    res0 = sf.funm(P, "sqrt", dev(A.val), F0, steps=25, residual=True)
+    assert res64 <= res0 and res <= 3 * res0
+
+
+def test_mixed_exp_double_squarings(sphere):
+    from paper_2211_11681_gb300 import sformat as sf
+    c, levels = sphere
+    A = c.A.like(c.A.val * 12.0)
+    P = pattern_of(A, levels)
+    F = dev(np.zeros(len(A.val)))
+    sf.funm(P, "exp_neg", dev(A.val), F, prec="fp32")
+    E = ofunm.expm_taylor(A, sign=-1.0, nthreads=8)
+    assert rel_frob(host(F), E.val) <= 1e-5
