@@ -323,6 +323,7 @@ def main():
     b, pat, vals, prep = build_input(w, n)
     t0 = time.time()
     plan32 = sf.Plan(pat, pat, pat, "fp32")
+    plan32.set_symmetric_a(True)      # A = T K T^T (+ mu I) is symmetric
     triples, flops = plan32.stats()
     prep["plan_s"] = round(time.time() - t0, 2)
     A32 = vals.float()
@@ -379,7 +380,20 @@ def main():
         err = float((C32.double() - C64).norm() / C64.norm())
         fp64 = {"ms": round(ms64, 3), "gflops": flops / (ms64 * 1e-3) / 1e9,
                 "mixed_rel_frob_err_vs_fp64": err, "mixed_speedup_vs_fp64": ms64 / ms}
-        del C64, plan64
+        # double-float (float-pair) product: double-accurate, on the float pipes
+        plandf = sf.Plan(pat, pat, pat, "fp64_df")
+        Cdf = torch.empty_like(vals)
+        plandf.mul(vals, vals, Cdf)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        plandf.mul(vals, vals, Cdf)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        msdf = e0.elapsed_time(e1)
+        fp64["fp64_df"] = {"ms": round(msdf, 3), "gflops": flops / (msdf * 1e-3) / 1e9,
+                           "rel_frob_err_vs_fp64": float((Cdf - C64).norm() / C64.norm()),
+                           "speedup_vs_fp64": ms64 / msdf}
+        del C64, plan64, Cdf, plandf
         torch.cuda.empty_cache()
 
     # end to end through the C ABI with host buffers (pinned), copies inside the region
@@ -418,7 +432,8 @@ def main():
         "fp64": fp64,
         "roofline": {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
                      "frac": achieved / fp32_peak, "traffic": kernel_traffic(),
-                     "kernel": "sf::mul_kernel<float,false,false>",
+                     "kernel": "sf::mul_f32_kernel<%d,%d,%d,true,false>" % (
+                         plan32.variant()["tile"], *plan32.variant()["micro"]),
                      "peak_source": "152 SMs x 128 FP32 lanes x 2 flop x sm_max_mhz (derived)"},
         "clocks": clocks,
         "e2e": e2e,

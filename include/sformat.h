@@ -115,6 +115,12 @@ s_status s_plan_autotune(s_plan plan, const void* A, const void* B, void* C, voi
  * product by hand (S_FP32 plans only). */
 s_status s_plan_set_variant(s_plan plan, int variant);
 int s_plan_num_variants(void);
+/* Declares that A's values are symmetric (A(nu, lambda) = A(lambda, nu)^T, as for a kernel
+ * matrix in samplet coordinates).  The forward product then reads A(nu, lambda) through the
+ * stored block (lambda, nu), which the float kernel stages with contiguous 16-byte copies.
+ * Checks that A's pattern is symmetric (S_ERR_PATTERN otherwise); the values are the
+ * caller's promise.  symmetric = 0 restores the default. */
+s_status s_plan_set_symmetric_a(s_plan plan, int symmetric);
 /* Shape of a float variant (variant < 0: the plan's current one): tile edge and micro-tile. */
 s_status s_plan_variant(s_plan plan, int variant, int* tile, int* micro_rows, int* micro_cols);
 

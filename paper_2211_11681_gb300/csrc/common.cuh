@@ -80,6 +80,8 @@ struct MulDesc {
   int64_t ntiles = 0;
   int edge = 20;             // tile edge of the list
   int variant = 0;           // float kernel variant (autotuned)
+  float2* df_x = nullptr;    // S_FP64_DF: split operands (hi, lo)
+  float2* df_y = nullptr;
   unsigned int* counter = nullptr;  // device work counter
   int64_t triples = 0;
   double flops = 0.0;

@@ -157,8 +157,11 @@ extern "C" s_status s_funm(s_pattern p, s_fn fn, const double* A, double* F, con
   s_funm_opts o = {};
   if (opts) o = *opts;
   const s_prec prec = o.prec;
-  if (prec != S_FP64 && prec != S_FP32) return set_error(S_ERR_ARG, "s_funm: prec must be S_FP64 or S_FP32");
-  const size_t w = prec == S_FP64 ? sizeof(double) : sizeof(float);
+  if (prec != S_FP64 && prec != S_FP32 && prec != S_FP64_DF)
+    return set_error(S_ERR_ARG, "s_funm: prec must be S_FP64, S_FP64_DF or S_FP32");
+  // iterates are double for S_FP64 and S_FP64_DF (products in double-float), float for S_FP32
+  const s_prec aprec = prec == S_FP32 ? S_FP32 : S_FP64;
+  const size_t w = aprec == S_FP64 ? sizeof(double) : sizeof(float);
   const int64_t nnz = p->d.nnz;
   s_plan plan = nullptr;
   s_status s = s_plan_create(p, p, p, prec, &plan);
@@ -186,25 +189,25 @@ extern "C" s_status s_funm(s_pattern p, s_fn fn, const double* A, double* F, con
     SyncOnExit sync{st};
     void *Y = bY.p, *Z = bZ.p, *T = bT.p, *P = bP.p;
     const void* Ain = A;
-    if (prec == S_FP32) {
+    if (aprec == S_FP32) {
       SF_CUDA(cudaMalloc(&bA.p, w * nnz + 16));
       convert_kernel<double, float><<<g, 256, 0, st>>>(nnz, A, (float*)bA.p, 1.0);
       Ain = bA.p;
     }
     // Y_0 = A / c, Z_0 = I
-    if ((s = run_add(p, prec, 1.0 / c, Ain, 0.0, nullptr, 0.0, Y, st))) return s;
+    if ((s = run_add(p, aprec, 1.0 / c, Ain, 0.0, nullptr, 0.0, Y, st))) return s;
     SF_CUDA(cudaMemsetAsync(Z, 0, w * nnz, st));
-    if ((s = run_add(p, prec, 1.0, Z, 0.0, nullptr, 1.0, Z, st))) return s;
+    if ((s = run_add(p, aprec, 1.0, Z, 0.0, nullptr, 1.0, Z, st))) return s;
     const int refine = std::max(0, o.refine);
     for (int k = 0; k < steps; ++k) {
-      if (o.checkpoints && prec == S_FP64) {
+      if (o.checkpoints && aprec == S_FP64) {
         double* ck = (double*)o.checkpoints + (int64_t)2 * k * nnz;
         SF_CUDA(cudaMemcpyAsync(ck, Y, w * nnz, cudaMemcpyDeviceToDevice, st));
         SF_CUDA(cudaMemcpyAsync(ck + nnz, Z, w * nnz, cudaMemcpyDeviceToDevice, st));
       }
       if ((s = run_mul(plan->fwd, prec, Z, Y, P, st))) return s;                 // P = P_S(Z Y)
-      if ((s = run_add(p, prec, -0.5, P, 0.0, nullptr, 1.5, T, st))) return s;   // T = (3I - P)/2
-      if (prec == S_FP64)
+      if ((s = run_add(p, aprec, -0.5, P, 0.0, nullptr, 1.5, T, st))) return s;   // T = (3I - P)/2
+      if (aprec == S_FP64)
         dist_to_identity_kernel<double><<<1, 1024, 0, st>>>(nnz, (const double*)T, p->d.nc, p->d.diag, p->d.bsize,
                                                             p->d.voff, (double)p->d.n, (double*)bN.p + k);
       else
@@ -217,8 +220,8 @@ extern "C" s_status s_funm(s_pattern p, s_fn fn, const double* A, double* F, con
     }
     const double sc = std::sqrt(c);
     if (refine == 0) {
-      if (prec == S_FP64) {
-        if ((s = run_add(p, prec, sc, Y, 0.0, nullptr, 0.0, F, st))) return s;
+      if (aprec == S_FP64) {
+        if ((s = run_add(p, aprec, sc, Y, 0.0, nullptr, 0.0, F, st))) return s;
       } else {
         convert_kernel<float, double><<<g, 256, 0, st>>>(nnz, (const float*)Y, F, sc);
         SF_CUDA(cudaGetLastError());
@@ -237,7 +240,7 @@ extern "C" s_status s_funm(s_pattern p, s_fn fn, const double* A, double* F, con
       SF_CUDA(cudaMalloc(&dW.p, b8));
       SyncOnExit sync64{st};
       double *Y8 = (double*)dY.p, *Z8 = (double*)dZ.p, *R8 = (double*)dR.p, *W8 = (double*)dW.p;
-      if (prec == S_FP64) {
+      if (aprec == S_FP64) {
         SF_CUDA(cudaMemcpyAsync(Y8, Y, b8 - 16, cudaMemcpyDeviceToDevice, st));
         SF_CUDA(cudaMemcpyAsync(Z8, Z, b8 - 16, cudaMemcpyDeviceToDevice, st));
       } else {
@@ -299,17 +302,17 @@ extern "C" s_status s_funm(s_pattern p, s_fn fn, const double* A, double* F, con
     SyncOnExit sync{st};
     void *X = bX.p, *E = bE.p, *W = bW.p;
     const double xs = sign / std::ldexp(1.0, sq);
-    if (prec == S_FP64) {
-      if ((s = run_add(p, prec, xs, A, 0.0, nullptr, 0.0, X, st))) return s;
+    if (aprec == S_FP64) {
+      if ((s = run_add(p, aprec, xs, A, 0.0, nullptr, 0.0, X, st))) return s;
     } else {
       convert_kernel<double, float><<<g, 256, 0, st>>>(nnz, A, (float*)X, xs);
     }
-    if ((s = run_add(p, prec, 1.0 / m, X, 0.0, nullptr, 1.0, E, st))) return s;   // E = I + X/m
+    if ((s = run_add(p, aprec, 1.0 / m, X, 0.0, nullptr, 1.0, E, st))) return s;   // E = I + X/m
     for (int k = m - 1; k >= 1; --k) {
       if ((s = run_mul(plan->fwd, prec, X, E, W, st))) return s;                   // W = P_S(X E)
-      if ((s = run_add(p, prec, 1.0 / k, W, 0.0, nullptr, 1.0, E, st))) return s; // E = I + W/k
+      if ((s = run_add(p, aprec, 1.0 / k, W, 0.0, nullptr, 1.0, E, st))) return s; // E = I + W/k
     }
-    if (prec == S_FP64) {
+    if (aprec == S_FP64) {
       for (int r = 0; r < sq; ++r) {
         if ((s = run_mul(plan->fwd, prec, E, E, W, st))) return s;                 // E = P_S(E E)
         std::swap(E, W);

@@ -262,10 +262,22 @@ __device__ __forceinline__ void stage_copy(const Stage& sg, const float* __restr
   const float* xb = X + xvoff[sg.bx];
   const float* yb = Y + yvoff[sg.by];
   const float rtk = 1.0f / (float)tk;
-  for (int e = lane; e < th * tk; e += 32) {
-    const int r = __float2int_rz(((float)e + 0.5f) * rtk), tt = e - r * tk;
-    const int gr = r0 + r, gt = t0 + tt;
-    cp_async4(xs + tt * TT + r, TX ? xb + (int64_t)gt * ni + gr : xb + (int64_t)gr * nl + gt);
+  const bool xvec = TX && r0 == 0 && th == ni && (ni & 3) == 0 && ((reinterpret_cast<uintptr_t>(xb) & 15) == 0);
+  if (xvec) {
+    // op(X) = X^T: row t of the stored block (lambda, nu) is column t of op(X), i.e. one
+    // contiguous run of sA[t][.]
+    const float rni = 1.0f / (float)ni;
+    for (int q = lane; q < (tk * ni) >> 2; q += 32) {
+      const int e = q << 2;
+      const int tt = __float2int_rz(((float)e + 0.5f) * rni), r = e - tt * ni;
+      cp_async16(xs + tt * TT + r, xb + (int64_t)(t0 + tt) * ni + r);
+    }
+  } else {
+    for (int e = lane; e < th * tk; e += 32) {
+      const int r = __float2int_rz(((float)e + 0.5f) * rtk), tt = e - r * tk;
+      const int gr = r0 + r, gt = t0 + tt;
+      cp_async4(xs + tt * TT + r, TX ? xb + (int64_t)gt * ni + gr : xb + (int64_t)gr * nl + gt);
+    }
   }
   const bool vec = !TY && c0 == 0 && tw == nj && (nj & 3) == 0 && ((reinterpret_cast<uintptr_t>(yb) & 15) == 0);
   if (vec) {
@@ -367,7 +379,7 @@ __global__ void __launch_bounds__(kF32Warps * 32, 4) mul_f32_kernel(MulArgs a, c
         if (active) {
           const float* xs = sA[w][buf];
           const float* ys = sB[w][buf];
-          for (int tt = 0; tt < tk; ++tt) {
+          auto step = [&](int tt) {
             float ar[MR], br[MC];
             lds<MR>(xs + tt * TT + rl, ar);
             lds<MC>(ys + tt * TT + cl, br);
@@ -375,6 +387,12 @@ __global__ void __launch_bounds__(kF32Warps * 32, 4) mul_f32_kernel(MulArgs a, c
             for (int ii = 0; ii < MR; ++ii)
 #pragma unroll
               for (int jj = 0; jj < MC; ++jj) p[ii * MC + jj] = fmaf(ar[ii], br[jj], p[ii * MC + jj]);
+          };
+          if (tk == TT) {
+#pragma unroll
+            for (int tt = 0; tt < TT; ++tt) step(tt);
+          } else {
+            for (int tt = 0; tt < tk; ++tt) step(tt);
           }
         }
         __syncwarp();
@@ -407,6 +425,187 @@ __global__ void __launch_bounds__(kF32Warps * 32, 4) mul_f32_kernel(MulArgs a, c
           const float err = (acc[qq] - (hi - bp)) + (p[qq] - bp);
           const int r = rl + ii, c = cl + jj;
           if (r < th && c < tw) cb[(int64_t)(tile.r0 + r) * nj + tile.c0 + c] = hi + (comp[qq] + err);
+        }
+    }
+  }
+}
+
+// Double-float product (S_FP64_DF): double operands arrive pre-split into float pairs
+// (hi, lo) with hi + lo = a to 2^-48; each term a*b is formed as the exact float product
+// hi*hi (fmaf recovers its rounding error) plus the cross terms hi*lo + lo*hi, and added
+// to the lambda block's float-pair partial with an error-free two-sum (~12 float
+// instructions per multiply-add).  At the end of each lambda block the partial is added to
+// the running float-pair total by a full pair addition with renormalisation, so the
+// rounding of the low words grows with the number of lambda blocks, not of terms.  Same
+// tiling, listing and cp.async streaming as the float kernel; tiles of 20 with 4x4
+// micro-tiles; shared memory is dynamic (float2).
+__global__ void split_kernel(int64_t n, const double* __restrict__ a, float2* __restrict__ out) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const double v = a[i];
+    const float hi = __double2float_rn(v);
+    out[i] = make_float2(hi, __double2float_rn(v - (double)hi));
+  }
+}
+
+__device__ __forceinline__ void cp_async8(float2* dst, const float2* src) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(d), "l"(src));
+}
+
+template <bool TX, bool TY>
+__device__ __forceinline__ void stage_copy_df(const Stage& sg, const float2* __restrict__ X,
+                                              const float2* __restrict__ Y, const int64_t* xvoff,
+                                              const int64_t* yvoff, int ni, int nj, int r0, int c0, int th, int tw,
+                                              int lane, float2* xs, float2* ys) {
+  constexpr int TT = kTile;
+  const int nl = sg.nl, t0 = sg.t0;
+  const int tk = min(TT, nl - t0);
+  const float2* xb = X + xvoff[sg.bx];
+  const float2* yb = Y + yvoff[sg.by];
+  const float rtk = 1.0f / (float)tk, rtw = 1.0f / (float)tw;
+  for (int e = lane; e < th * tk; e += 32) {
+    const int r = __float2int_rz(((float)e + 0.5f) * rtk), tt = e - r * tk;
+    const int gr = r0 + r, gt = t0 + tt;
+    cp_async8(xs + tt * TT + r, TX ? xb + (int64_t)gt * ni + gr : xb + (int64_t)gr * nl + gt);
+  }
+  for (int e = lane; e < tk * tw; e += 32) {
+    const int tt = __float2int_rz(((float)e + 0.5f) * rtw), c = e - tt * tw;
+    const int gt = t0 + tt, gc = c0 + c;
+    cp_async8(ys + tt * TT + c, TY ? yb + (int64_t)gc * nl + gt : yb + (int64_t)gt * nj + gc);
+  }
+}
+
+constexpr int kDfWarps = 4;
+constexpr size_t kDfSmem = sizeof(float2) * kDfWarps * 2 * 2 * kTile * kTile;  // [warp][buf][A|B][TT*TT]
+
+template <bool TX, bool TY>
+__global__ void __launch_bounds__(kDfWarps * 32, 3) mul_df_kernel(MulArgs a, const float2* __restrict__ X,
+                                                                  const float2* __restrict__ Y,
+                                                                  double* __restrict__ C) {
+  constexpr int TT = kTile, MR = 4, MC = 4, GC = TT / MC, NA = (TT / MR) * GC;
+  extern __shared__ __align__(16) float2 dsm[];
+  __shared__ Stage sStage[kDfWarps][kStages];
+  const int lane = threadIdx.x & 31;
+  const int w = threadIdx.x >> 5;
+  float2* base = dsm + (size_t)w * 4 * TT * TT;  // [buf0: A, B][buf1: A, B]
+  Stage* st = sStage[w];
+  const bool active = lane < NA;
+  const int mr = active ? lane / GC : 0, mc = active ? lane % GC : 0;
+  const int rl = MR * mr, cl = MC * mc;
+  for (;;) {
+    unsigned int t = 0;
+    if (lane == 0) t = atomicAdd(a.counter, 1u);
+    t = __shfl_sync(0xffffffffu, t, 0);
+    if (t >= a.ntiles) break;
+    const Tile tile = a.tiles[t];
+    const int k = tile.blk;
+    const int nu = a.c_brow[k], nup = a.c_col[k];
+    const int ni = a.bsize[nu], nj = a.bsize[nup];
+    const int th = min(TT, ni - tile.r0), tw = min(TT, nj - tile.c0);
+    float sh[16], sl[16], ph[16], pl[16];  // running total and lambda-block partial
+#pragma unroll
+    for (int q = 0; q < 16; ++q) sh[q] = sl[q] = ph[q] = pl[q] = 0.0f;
+    const int px1 = (int)a.x.ptr[nu + 1];
+    int px = (int)a.x.ptr[nu];
+    int py0 = (int)a.y.ptr[nup];
+    const int py1 = (int)a.y.ptr[nup + 1];
+    while (px < px1 && py0 < py1) {
+      int nm = 0;
+      while (px < px1 && py0 < py1 && nm <= kStages - 32) {
+        const int i = px + lane;
+        const int32_t lam = i < px1 ? __ldg(a.x.idx + i) : INT32_MAX;
+        const int pos = lower_bound_dev(a.y.idx, py0, py1, lam);
+        const bool hit = i < px1 && pos < py1 && __ldg(a.y.idx + pos) == lam;
+        const unsigned int mask = __ballot_sync(0xffffffffu, hit);
+        if (hit) {
+          const int kx = a.x.blk ? __ldg(a.x.blk + i) : i;
+          const int ky = a.y.blk ? __ldg(a.y.blk + pos) : pos;
+          st[nm + __popc(mask & ((1u << lane) - 1u))] = Stage{kx, ky, (int16_t)a.bsize[lam], 0};
+        }
+        nm += __popc(mask);
+        py0 = __shfl_sync(0xffffffffu, pos, 31);
+        px += 32;
+      }
+      __syncwarp();
+      if (nm == 0) continue;
+      int m = 0, q = 0, buf = 0;
+      stage_copy_df<TX, TY>(st[0], X, Y, a.x.voff, a.y.voff, ni, nj, tile.r0, tile.c0, th, tw, lane, base,
+                            base + TT * TT);
+      cp_commit();
+      for (;;) {
+        const Stage cur = st[m];
+        const int t0 = q * TT;
+        const bool last_slice = t0 + TT >= (int)cur.nl;
+        const int nm2 = last_slice ? m + 1 : m, nq2 = last_slice ? 0 : q + 1;
+        const bool more = nm2 < nm;
+        if (more) {
+          Stage sg = st[nm2];
+          sg.t0 = (int16_t)(nq2 * TT);
+          float2* nb = base + (buf ^ 1) * 2 * TT * TT;
+          stage_copy_df<TX, TY>(sg, X, Y, a.x.voff, a.y.voff, ni, nj, tile.r0, tile.c0, th, tw, lane, nb,
+                                nb + TT * TT);
+          cp_commit();
+          cp_wait<1>();
+        } else {
+          cp_wait<0>();
+        }
+        __syncwarp();
+        const int tk = min(TT, (int)cur.nl - t0);
+        if (active) {
+          const float2* xs = base + buf * 2 * TT * TT;
+          const float2* ys = xs + TT * TT;
+          for (int tt = 0; tt < tk; ++tt) {
+            float2 av[4], bv[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+              av[u] = xs[tt * TT + rl + u];
+              bv[u] = ys[tt * TT + cl + u];
+            }
+#pragma unroll
+            for (int ii = 0; ii < 4; ++ii)
+#pragma unroll
+              for (int jj = 0; jj < 4; ++jj) {
+                const int qq = ii * 4 + jj;
+                const float p = av[ii].x * bv[jj].x;
+                float e = fmaf(av[ii].x, bv[jj].x, -p);
+                e = fmaf(av[ii].x, bv[jj].y, e);
+                e = fmaf(av[ii].y, bv[jj].x, e);
+                const float hi = ph[qq] + p;
+                const float bp = hi - ph[qq];
+                pl[qq] += ((ph[qq] - (hi - bp)) + (p - bp)) + e;
+                ph[qq] = hi;
+              }
+          }
+        }
+        __syncwarp();
+        if (last_slice) {
+          // (sh, sl) += (ph, pl): two-sum of the high words, low words added, renormalised
+#pragma unroll
+          for (int qq = 0; qq < 16; ++qq) {
+            const float s1 = sh[qq] + ph[qq];
+            const float bp = s1 - sh[qq];
+            const float e1 = ((sh[qq] - (s1 - bp)) + (ph[qq] - bp)) + (sl[qq] + pl[qq]);
+            const float s2 = s1 + e1;
+            sl[qq] = e1 - (s2 - s1);
+            sh[qq] = s2;
+            ph[qq] = pl[qq] = 0.0f;
+          }
+        }
+        if (!more) break;
+        m = nm2;
+        q = nq2;
+        buf ^= 1;
+      }
+    }
+    if (active) {
+      double* cb = C + a.c_voff[k];
+#pragma unroll
+      for (int ii = 0; ii < 4; ++ii)
+#pragma unroll
+        for (int jj = 0; jj < 4; ++jj) {
+          const int r = rl + ii, c = cl + jj;
+          if (r < th && c < tw)
+            cb[(int64_t)(tile.r0 + r) * nj + tile.c0 + c] = (double)sh[ii * 4 + jj] + (double)sl[ii * 4 + jj];
         }
     }
   }
@@ -519,6 +718,12 @@ s_status build_desc(const s_pattern_t* X, bool tx, const s_pattern_t* Y, bool ty
   cudaFree(bflops);
   if (e != cudaSuccess) st = cuda_error(e, "s_plan_create(symbolic)");
   if (!st) st = build_tiles(&d, kF32Variants[0].tt);
+  if (!st && prec == S_FP64_DF) {
+    // split operands (float pairs), reused by every call of this plan
+    e = cudaMalloc(&d.df_x, sizeof(float2) * std::max<int64_t>(X->d.nnz, 1));
+    if (e == cudaSuccess) e = cudaMalloc(&d.df_y, sizeof(float2) * std::max<int64_t>(Y->d.nnz, 1));
+    if (e != cudaSuccess) st = cuda_error(e, "cudaMalloc(double-float scratch)");
+  }
   if (st) {
     free_desc(&d);
     return st;
@@ -530,6 +735,9 @@ s_status build_desc(const s_pattern_t* X, bool tx, const s_pattern_t* Y, bool ty
 void free_desc(MulDesc* d) {
   cudaFree(d->tiles);
   cudaFree(d->counter);
+  cudaFree(d->df_x);
+  cudaFree(d->df_y);
+  d->df_x = d->df_y = nullptr;
   d->tiles = nullptr;
   d->counter = nullptr;
   d->ntiles = 0;
@@ -590,12 +798,52 @@ static s_status launch_typed(const MulDesc& d, const void* X, const void* Y, voi
   return S_OK;
 }
 
+static s_status launch_df(const MulDesc& d, const void* X, const void* Y, void* C, cudaStream_t st) {
+  if (d.ntiles == 0) return S_OK;
+  if (d.edge != kTile) return set_error(S_ERR_ARG, "internal: double-float kernel needs 20-wide tiles");
+  if (!d.df_x || !d.df_y) return set_error(S_ERR_ARG, "internal: double-float scratch missing");
+  const int64_t nx = d.px->d.nnz, ny = d.py->d.nnz;
+  const int gx = (int)std::max<int64_t>(1, std::min<int64_t>((nx + 255) / 256, (int64_t)num_sms() * 16));
+  const int gy = (int)std::max<int64_t>(1, std::min<int64_t>((ny + 255) / 256, (int64_t)num_sms() * 16));
+  if (nx) split_kernel<<<gx, 256, 0, st>>>(nx, (const double*)X, d.df_x);
+  const float2* ysplit = d.df_x;
+  if (Y != X || d.px != d.py) {
+    if (ny) split_kernel<<<gy, 256, 0, st>>>(ny, (const double*)Y, d.df_y);
+    ysplit = d.df_y;
+  }
+  MulArgs a;
+  a.x = dev_side(d.x);
+  a.y = dev_side(d.y);
+  a.bsize = d.pc->d.bsize;
+  a.c_brow = d.pc->d.brow;
+  a.c_col = d.pc->d.colidx;
+  a.c_voff = d.pc->d.voff;
+  a.tiles = d.tiles;
+  a.ntiles = d.ntiles;
+  a.counter = d.counter;
+  SF_CUDA(cudaMemsetAsync(d.counter, 0, sizeof(unsigned int), st));
+  using K = void (*)(MulArgs, const float2*, const float2*, double*);
+  K kern = d.x.trans ? (d.y.trans ? mul_df_kernel<true, true> : mul_df_kernel<true, false>)
+                     : (d.y.trans ? mul_df_kernel<false, true> : mul_df_kernel<false, false>);
+  SF_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kDfSmem));
+  int per_sm = 0;
+  SF_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kDfWarps * 32, kDfSmem));
+  if (per_sm < 1) per_sm = 1;
+  const int64_t want = (d.ntiles + kDfWarps - 1) / kDfWarps;
+  const int grid = (int)std::min<int64_t>(want, (int64_t)num_sms() * per_sm);
+  kern<<<grid, kDfWarps * 32, kDfSmem, st>>>(a, d.df_x, ysplit, (double*)C);
+  SF_CUDA(cudaGetLastError());
+  return S_OK;
+}
+
 s_status run_mul(const MulDesc& d, s_prec prec, const void* X, const void* Y, void* C, cudaStream_t st) {
   switch (prec) {
     case S_FP64:
       return launch_typed<double>(d, X, Y, C, st);
     case S_FP32:
       return launch_typed<float>(d, X, Y, C, st);
+    case S_FP64_DF:
+      return launch_df(d, X, Y, C, st);
     default:
       return set_error(S_ERR_ARG, "precision not supported by this product path");
   }
@@ -615,7 +863,8 @@ extern "C" s_status s_plan_create(s_pattern A, s_pattern B, s_pattern C, s_prec 
   if (!out) return set_error(S_ERR_ARG, "s_plan_create: out is NULL");
   *out = nullptr;
   if (!A || !B || !C) return set_error(S_ERR_ARG, "s_plan_create: NULL pattern");
-  if (prec != S_FP64 && prec != S_FP32) return set_error(S_ERR_ARG, "s_plan_create: unsupported precision");
+  if (prec != S_FP64 && prec != S_FP32 && prec != S_FP64_DF)
+    return set_error(S_ERR_ARG, "s_plan_create: unsupported precision (S_FP64, S_FP32 or S_FP64_DF)");
   s_status st;
   if ((st = check_same_tree(A, B)) || (st = check_same_tree(A, C))) return st;
   s_plan_t* p = new (std::nothrow) s_plan_t();
@@ -745,3 +994,28 @@ extern "C" s_status s_plan_set_variant(s_plan p, int variant) {
 }
 
 extern "C" int s_plan_num_variants(void) { return kNumF32Variants; }
+
+extern "C" s_status s_plan_set_symmetric_a(s_plan p, int symmetric) {
+  if (!p) return set_error(S_ERR_ARG, "s_plan_set_symmetric_a: NULL plan");
+  const s_pattern_t* A = p->a;
+  if (symmetric) {
+    // the pattern must be symmetric: CSR and CSC index lists coincide
+    if (A->rowptr.size() < 2) return S_OK;
+    std::vector<int64_t> cnt(A->d.nc + 1, 0);
+    for (int32_t c : A->colidx) cnt[c + 1]++;
+    for (int32_t i = 0; i < A->d.nc; ++i)
+      if (cnt[i + 1] != A->rowptr[i + 1] - A->rowptr[i])
+        return set_error(S_ERR_PATTERN, "s_plan_set_symmetric_a: the pattern of A is not symmetric");
+    for (int32_t i = 0; i < A->d.nc; ++i)
+      for (int64_t k = A->rowptr[i]; k < A->rowptr[i + 1]; ++k) {
+        const int32_t j = A->colidx[k];
+        auto b = A->colidx.begin() + A->rowptr[j], e = A->colidx.begin() + A->rowptr[j + 1];
+        if (!std::binary_search(b, e, i))
+          return set_error(S_ERR_PATTERN, "s_plan_set_symmetric_a: the pattern of A is not symmetric");
+      }
+  }
+  // read A(nu, lambda) as the transpose of the stored block (lambda, nu): same values when A
+  // is symmetric, and column-contiguous staging for the float kernel
+  p->fwd.x = side_of(A, true, symmetric != 0);
+  return S_OK;
+}

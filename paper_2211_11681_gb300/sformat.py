@@ -46,6 +46,7 @@ def _load():
         "s_plan_autotune": (i32, [vp, vp, vp, vp, vp, P(i32)]),
         "s_plan_variant": (i32, [vp, i32, P(i32), P(i32), P(i32)]),
         "s_plan_set_variant": (i32, [vp, i32]),
+        "s_plan_set_symmetric_a": (i32, [vp, i32]),
         "s_plan_num_variants": (i32, []),
         "s_pattern_concat": (i32, [i32, P(vp), P(vp)]),
         "s_graph_capture_mul": (i32, [vp, vp, vp, vp, P(vp)]),
@@ -182,6 +183,10 @@ class Plan:
         check(lib.s_plan_autotune(self.h, _ptr(A), _ptr(B), _ptr(C), _stream(stream), ctypes.byref(v)))
         self.variant_index = v.value
         return self.variant()
+
+    def set_symmetric_a(self, flag=True):
+        """Caller asserts A is symmetric; the product reads A through its transposed index."""
+        check(lib.s_plan_set_symmetric_a(self.h, 1 if flag else 0))
 
     def set_variant(self, v):
         check(lib.s_plan_set_variant(self.h, int(v)))

@@ -35,6 +35,9 @@ def test_sqrt_parity(sphere):
     X = ofunm.sqrtm_ns(A, steps=25, nthreads=8)
     assert rel_frob(host(F), X.val) <= 1e-10
     assert res == pytest.approx(ofunm.sqrt_residual(X, A, nthreads=8), rel=1e-6)
+    Fdf = dev(np.zeros(len(A.val)))
+    sf.funm(P, "sqrt", dev(A.val), Fdf, steps=25, prec="fp64_df")
+    assert rel_frob(host(Fdf), X.val) <= 1e-10
     F32 = dev(np.zeros(len(A.val)))
     res32 = sf.funm(P, "sqrt", dev(A.val), F32, steps=25, prec="fp32", residual=True)
     assert rel_frob(host(F32), X.val) <= 1e-5

@@ -1,5 +1,6 @@
 """GPU parity of the masked product (Eq. (product)), its adjoint, S-format addition and the
-norm estimate against the FP64 CPU oracle, through the C ABI.
+norm estimate against the FP64 CPU oracle, through the C ABI, in double, double-float
+(S_FP64_DF) and compensated float arithmetic.
 
 Tolerances: FP64 results agree with the oracle to 1e-12 relative Frobenius error (the
 summation order differs, each entry is a sum of at most a few thousand products of
@@ -56,6 +57,12 @@ def test_c1_fp64_parity(sf, c1):
     dC2 = dev(np.zeros(len(A.val)))
     plan.mul(dA, dA, dC2)
     np.testing.assert_array_equal(host(dC2), got)
+    # double-float arithmetic (float pairs, ~2^-44 per term) meets the double bound too
+    pdf = sf.Plan(P, P, P, "fp64_df")
+    assert pdf.stats() == (t, f)
+    dD = dev(np.full(len(A.val), np.nan))
+    pdf.mul(dA, dA, dD)
+    assert rel_frob(host(dD), want) <= 1e-12
 
 
 @pytest.mark.parametrize("seed", [1, 2, 3, 4])
@@ -81,6 +88,11 @@ def test_general_patterns_and_ragged_tiles(sf, seed):
     o32 = dev(np.zeros(len(Cp.val)), "float32")
     p32.mul(dev(A.val, "float32"), dev(B.val, "float32"), o32)
     assert rel_frob(host(o32), want) <= 1e-5
+    # double-float arithmetic, forward and adjoint
+    pdf = sf.Plan(pa, pb, pc, "fp64_df")
+    odf = dev(np.full(len(Cp.val), np.nan))
+    pdf.mul(dev(A.val), dev(B.val), odf)
+    assert rel_frob(host(odf), want) <= 1e-12
     # adjoint
     dC = Cp.like(W.random_values(len(Cp.val), seed + 99))
     gA, gB = dev(np.zeros(len(A.val))), dev(np.zeros(len(B.val)))
@@ -88,6 +100,10 @@ def test_general_patterns_and_ragged_tiles(sf, seed):
     wA, wB = oadj.mul_masked_adjoint(dC, A, B)
     assert rel_frob(host(gA), wA.val) <= 1e-12
     assert rel_frob(host(gB), wB.val) <= 1e-12
+    hA, hB = dev(np.zeros(len(A.val))), dev(np.zeros(len(B.val)))
+    pdf.adjoint(dev(dC.val), dev(A.val), dev(B.val), hA, hB)
+    assert rel_frob(host(hA), wA.val) <= 1e-12
+    assert rel_frob(host(hB), wB.val) <= 1e-12
 
 
 def drop_empty(X):
@@ -115,6 +131,14 @@ def test_c1_fp32_error_and_add(sf, c1):
     plan.mul(dev(A.val, "float32"), dev(A.val, "float32"), out)
     want = oprod.mul_masked(A, A, A, nthreads=8).val
     assert rel_frob(host(out), want) <= 1e-6          # the mixed-precision target
+    # A is symmetric: reading A(nu, lambda) through the stored (lambda, nu) gives the same product
+    for prec, tol in (("fp32", 1e-6), ("fp64", 1e-12)):
+        ps = sf.Plan(P, P, P, prec)
+        ps.set_symmetric_a(True)
+        dt = "float32" if prec == "fp32" else "float64"
+        o = dev(np.zeros(len(A.val)), dt)
+        ps.mul(dev(A.val, dt), dev(A.val, dt), o)
+        assert rel_frob(host(o), want) <= tol
     B = A.like(W.random_values(len(A.val), 5))
     C = dev(np.zeros(len(A.val)))
     sf.add(P, dev(A.val), dev(B.val), C, 0.75, -2.0, 0.5)
@@ -135,6 +159,13 @@ def test_tree_mismatch_and_empty(sf, c1):
     with pytest.raises(sf.SFormatError) as e:
         sf.Plan(P, Q, P)
     assert e.value.status == sf.S_ERR_MISMATCH
+    # the symmetric flag checks the pattern
+    from oracle.sformat import BlockCSR as _B
+    asym = _B(c.A.bsize, np.array([0, 2] + [2] * (c.A.nclusters - 1)), np.array([0, 1]))
+    pa = pattern_of(asym, levels)
+    with pytest.raises(sf.SFormatError) as e2:
+        sf.Plan(pa, pa, pa).set_symmetric_a(True)
+    assert e2.value.status == sf.S_ERR_PATTERN
     # an empty output pattern is a valid, empty product
     from oracle.sformat import BlockCSR
     Z = BlockCSR(c.A.bsize, np.zeros(c.A.nclusters + 1, dtype=np.int64), np.zeros(0, dtype=np.int64))
