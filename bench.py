@@ -292,6 +292,56 @@ def run_batch(args, rank, world):
         print(json.dumps(line), flush=True)
 
 
+def run_drivers(args, rank, world):
+    """Matrix functions at full size (N = 2^18 points on the sphere, Matern-5/2, ell = 0.3,
+    nugget 1e-2, q = 2, eta = 1.25): A^{1/2} by 25 Newton-Schulz steps and exp(-A) by
+    Taylor-8 with scaling and squaring, in double, double-float and mixed precision (float
+    iterations with double residual correction / double squarings)."""
+    import torch
+    import workloads as W
+    from paper_2211_11681_gb300 import sformat as sf
+    w = W.WORKLOADS["matern52_sphere"]
+    n = args.n or w.n
+    b, pat, vals, prep = build_input(w, n)
+    plan = sf.Plan(pat, pat, pat, "fp64")
+    triples, flops = plan.stats()
+    lam = sf.norm_est(pat, vals, 50)
+    c = 1.01 * lam
+    out = {}
+    F = {}
+    for name, prec, refine in (("fp64", "fp64", 0), ("fp64_df", "fp64_df", 0), ("mixed", "fp32", 2)):
+        Fx = torch.empty_like(vals)
+        torch.cuda.synchronize()
+        t0 = time.time()
+        res = sf.funm(pat, "sqrt", vals, Fx, steps=25, prec=prec, scale=c, refine=refine, residual=True)
+        torch.cuda.synchronize()
+        out["sqrt_" + name] = {"s": round(time.time() - t0, 3), "residual": res,
+                               "products": 75 + 2 * refine}
+        F[name] = Fx
+    for name in ("fp64_df", "mixed"):
+        out["sqrt_" + name]["rel_frob_vs_fp64"] = float((F[name] - F["fp64"]).norm() / F["fp64"].norm())
+        out["sqrt_" + name]["speedup_vs_fp64"] = out["sqrt_fp64"]["s"] / out["sqrt_" + name]["s"]
+    E = {}
+    for name, prec in (("fp64", "fp64"), ("fp64_df", "fp64_df"), ("mixed", "fp32")):
+        Ex = torch.empty_like(vals)
+        torch.cuda.synchronize()
+        t0 = time.time()
+        sf.funm(pat, "exp_neg", vals, Ex, prec=prec, scale=lam)
+        torch.cuda.synchronize()
+        out["expneg_" + name] = {"s": round(time.time() - t0, 3)}
+        E[name] = Ex
+    for name in ("fp64_df", "mixed"):
+        out["expneg_" + name]["rel_frob_vs_fp64"] = float((E[name] - E["fp64"]).norm() / E["fp64"].norm())
+        out["expneg_" + name]["speedup_vs_fp64"] = out["expneg_fp64"]["s"] / out["expneg_" + name]["s"]
+    line = {"metric": "A^{1/2} (25 Newton-Schulz steps) and exp(-A) on S, N=%d sphere" % n,
+            "value": out["sqrt_mixed"]["s"], "unit": "s per A^{1/2} (mixed)", "higher_is_better": False,
+            "n_gpus": world, "dtype": "f32+f64", "data": "synthetic",
+            "config": dict(workload_config(w, n, pat, triples, flops), lambda_max=lam, prep_seconds=prep),
+            "drivers": out}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     import torch
@@ -304,6 +354,12 @@ def main():
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    if args.workload == "matern52_sphere":
+        run_drivers(args, rank, world)
+        if dist is not None:
+            dist.barrier()
+            dist.destroy_process_group()
+        return
     if args.workload == "matern32_2d_batch":
         run_batch(args, rank, world)
         if dist is not None:
@@ -393,7 +449,23 @@ def main():
         fp64["fp64_df"] = {"ms": round(msdf, 3), "gflops": flops / (msdf * 1e-3) / 1e9,
                            "rel_frob_err_vs_fp64": float((Cdf - C64).norm() / C64.norm()),
                            "speedup_vs_fp64": ms64 / msdf}
-        del C64, plan64, Cdf, plandf
+        del Cdf, plandf
+        # split-bfloat16 tensor-core product (float in and out)
+        planbf = sf.Plan(pat, pat, pat, "bf16x3")
+        planbf.set_symmetric_a(True)
+        Cbf = torch.empty_like(A32)
+        planbf.mul(A32, A32, Cbf)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(3):
+            planbf.mul(A32, A32, Cbf)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        msbf = e0.elapsed_time(e1) / 3
+        fp64["bf16x3"] = {"ms": round(msbf, 3), "gflops": flops / (msbf * 1e-3) / 1e9,
+                          "rel_frob_err_vs_fp64": float((Cbf.double() - C64).norm() / C64.norm()),
+                          "speedup_vs_fp64": ms64 / msbf}
+        del C64, plan64, Cbf, planbf
         torch.cuda.empty_cache()
 
     # end to end through the C ABI with host buffers (pinned), copies inside the region

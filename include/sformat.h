@@ -199,6 +199,9 @@ typedef struct {
  *              degree, Horner's rule on X = +-A/2^s, then s masked squarings,
  *              s = max(0, ceil(log2(lambda/0.5))).  With prec S_FP32 the Horner products
  *              run in float and the squarings in double.
+ * With prec S_FP32, S_SQRT autotunes the float product kernel's shape on A first
+ * (s_plan_autotune).  With prec S_FP64_DF the iterates are double and the products run in
+ * double-float arithmetic.
  * Synchronises the stream once (norm estimate) unless opts->scale is given. */
 s_status s_funm(s_pattern p, s_fn fn, const double* A, double* F, const s_funm_opts* opts, void* stream);
 

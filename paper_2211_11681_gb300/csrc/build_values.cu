@@ -63,8 +63,8 @@ __device__ __forceinline__ float matern(float r, int p, float inv_ell, float sca
 // K(rows i0.., chunk columns) into shared memory, then the column transforms of every
 // cluster of the chunk's subtree (bottom-up), then the tile to U (row-major N x w).
 __global__ void eval_colfwt_kernel(Geo g, int64_t n, int64_t q0, int w, const int32_t* sub, const int32_t* sub_lvl_off,
-                                   int nlev, int p, float inv_ell, float scale, float* U) {
-  extern __shared__ float tile[];  // kRowTile x w
+                                   int nlev, int p, float inv_ell, float scale, int maxm, float* U) {
+  extern __shared__ float tile[];  // kRowTile x w, then per warp Q (maxm^2) and slots (maxm)
   const int64_t i0 = (int64_t)blockIdx.x * kRowTile;
   const int rows = (int)min((int64_t)kRowTile, n - i0);
   for (int e = threadIdx.x; e < kRowTile * w; e += blockDim.x) {
@@ -80,26 +80,32 @@ __global__ void eval_colfwt_kernel(Geo g, int64_t n, int64_t q0, int w, const in
   }
   __syncthreads();
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+  // per warp: the cluster's Q (m x m) and slots, staged once and applied to every row
+  float* qs = tile + kRowTile * w + warp * (maxm * maxm + maxm);
+  int* ss = reinterpret_cast<int*>(qs + maxm * maxm);
   for (int L = 0; L < nlev; ++L) {  // sub is ordered deepest level first
     const int c0 = sub_lvl_off[L], c1 = sub_lvl_off[L + 1];
-    const int ntask = (c1 - c0) * rows;
-    for (int t = warp; t < ntask; t += nwarp) {
-      const int c = sub[c0 + t / rows];
-      const int r = t % rows;
+    for (int ci = c0 + warp; ci < c1; ci += nwarp) {
+      const int c = sub[ci];
       const int m = g.nin[c];
       const int32_t* sl = g.slots + g.slot_off[c];
       const float* Q = g.Q + g.qoff[c];
-      float* row = tile + r * w;
-      float o0 = 0.0f, o1 = 0.0f;
-      for (int ii = 0; ii < m; ++ii) {
-        const float in = row[sl[ii] - q0];
-        if (lane < m) o0 = fmaf(in, Q[ii * m + lane], o0);
-        if (lane + 32 < m) o1 = fmaf(in, Q[ii * m + lane + 32], o1);
+      for (int e = lane; e < m * m; e += 32) qs[e] = Q[e];
+      for (int e = lane; e < m; e += 32) ss[e] = sl[e] - (int)q0;
+      __syncwarp();
+      for (int r = 0; r < rows; ++r) {
+        float* row = tile + r * w;
+        float o0 = 0.0f, o1 = 0.0f;
+        for (int ii = 0; ii < m; ++ii) {
+          const float in = row[ss[ii]];
+          if (lane < m) o0 = fmaf(in, qs[ii * m + lane], o0);
+          if (lane + 32 < m) o1 = fmaf(in, qs[ii * m + lane + 32], o1);
+        }
+        __syncwarp();
+        if (lane < m) row[ss[lane]] = o0;
+        if (lane + 32 < m) row[ss[lane + 32]] = o1;
+        __syncwarp();
       }
-      __syncwarp();
-      if (lane < m) row[sl[lane] - q0] = o0;
-      if (lane + 32 < m) row[sl[lane + 32] - q0] = o1;
-      __syncwarp();
     }
     __syncthreads();
   }
@@ -378,7 +384,9 @@ static s_status values_impl(s_build b, double nu, double ell, double kscale, dou
   int32_t* dlvl;
   if ((st = upload(&dlvl, lvl_flat))) return st;
   fr.add(dlvl);
-  const size_t smem = sizeof(float) * kRowTile * wmax;
+  int maxm = 1;
+  for (const auto& c : b->cl) maxm = std::max(maxm, c.nin);
+  const size_t smem = sizeof(float) * ((size_t)kRowTile * wmax + 8 * (size_t)(maxm * maxm + maxm));
   SF_CUDA(cudaFuncSetAttribute(eval_colfwt_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   // scaling columns of finished clusters, waiting for their sibling: (cluster, N x ns buffer)
   std::vector<std::pair<int32_t, float*>> stack;
@@ -434,7 +442,7 @@ static s_status values_impl(s_build b, double nu, double ell, double kscale, dou
     int32_t *dsub, *dsuboff;
     if ((st = upload(&dsub, sub)) || (st = upload(&dsuboff, sub_off))) return st;
     eval_colfwt_kernel<<<(unsigned)((n + kRowTile - 1) / kRowTile), 256, smem>>>(
-        g, n, q0, w, dsub, dsuboff, (int)sub_off.size() - 1, p, (float)(1.0 / ell), (float)kscale, dU);
+        g, n, q0, w, dsub, dsuboff, (int)sub_off.size() - 1, p, (float)(1.0 / ell), (float)kscale, maxm, dU);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) {
       cudaFree(dsub);

@@ -82,6 +82,8 @@ struct MulDesc {
   int variant = 0;           // float kernel variant (autotuned)
   float2* df_x = nullptr;    // S_FP64_DF: split operands (hi, lo)
   float2* df_y = nullptr;
+  struct __nv_bfloat16* bf_x = nullptr;  // S_BF16X3: three bfloat16 planes per operand
+  struct __nv_bfloat16* bf_y = nullptr;
   unsigned int* counter = nullptr;  // device work counter
   int64_t triples = 0;
   double flops = 0.0;

@@ -193,6 +193,7 @@ extern "C" s_status s_funm(s_pattern p, s_fn fn, const double* A, double* F, con
       SF_CUDA(cudaMalloc(&bA.p, w * nnz + 16));
       convert_kernel<double, float><<<g, 256, 0, st>>>(nnz, A, (float*)bA.p, 1.0);
       Ain = bA.p;
+      if (prec == S_FP32 && (s = s_plan_autotune(plan, Ain, Ain, P, st, nullptr))) return s;  // kernel shape
     }
     // Y_0 = A / c, Z_0 = I
     if ((s = run_add(p, aprec, 1.0 / c, Ain, 0.0, nullptr, 0.0, Y, st))) return s;

@@ -8,6 +8,8 @@
 // row(op(X), nu) and col(op(Y), nu'); a warp intersects them 32 entries of the X list at a
 // time by binary search in the Y list.  Warps take tiles from a device counter
 // (persistent grid sized to the SM count); tiles follow the block order of S_C.
+#include <cuda_bf16.h>
+
 #include <algorithm>
 #include <cstring>
 #include <new>
@@ -262,7 +264,8 @@ __device__ __forceinline__ void stage_copy(const Stage& sg, const float* __restr
   const float* xb = X + xvoff[sg.bx];
   const float* yb = Y + yvoff[sg.by];
   const float rtk = 1.0f / (float)tk;
-  const bool xvec = TX && r0 == 0 && th == ni && (ni & 3) == 0 && ((reinterpret_cast<uintptr_t>(xb) & 15) == 0);
+  const bool xvec = TT % 4 == 0 && TX && r0 == 0 && th == ni && (ni & 3) == 0 &&
+                    ((reinterpret_cast<uintptr_t>(xb) & 15) == 0);
   if (xvec) {
     // op(X) = X^T: row t of the stored block (lambda, nu) is column t of op(X), i.e. one
     // contiguous run of sA[t][.]
@@ -279,7 +282,9 @@ __device__ __forceinline__ void stage_copy(const Stage& sg, const float* __restr
       cp_async4(xs + tt * TT + r, TX ? xb + (int64_t)gt * ni + gr : xb + (int64_t)gr * nl + gt);
     }
   }
-  const bool vec = !TY && c0 == 0 && tw == nj && (nj & 3) == 0 && ((reinterpret_cast<uintptr_t>(yb) & 15) == 0);
+  // 16-byte copies need 16-byte aligned shared rows: TT a multiple of 4
+  const bool vec = TT % 4 == 0 && !TY && c0 == 0 && tw == nj && (nj & 3) == 0 &&
+                   ((reinterpret_cast<uintptr_t>(yb) & 15) == 0);
   if (vec) {
     const float rnj = 1.0f / (float)nj;
     for (int q = lane; q < (tk * nj) >> 2; q += 32) {
@@ -302,7 +307,9 @@ __global__ void __launch_bounds__(kF32Warps * 32, 4) mul_f32_kernel(MulArgs a, c
                                                                     const float* __restrict__ Y,
                                                                     float* __restrict__ C) {
   constexpr int GR = TT / MR, GC = TT / MC, NA = GR * GC, NQ = MR * MC;
-  static_assert(TT % MR == 0 && TT % MC == 0 && NA <= 32 && TT % 4 == 0, "bad micro-tile");
+  static_assert(TT % MR == 0 && TT % MC == 0 && NA <= 32 && TT % 2 == 0 && (MR != 4 || TT % 4 == 0) &&
+                    (MC != 4 || TT % 4 == 0),
+                "bad micro-tile");
   __shared__ __align__(16) float sA[kF32Warps][2][TT * TT];
   __shared__ __align__(16) float sB[kF32Warps][2][TT * TT];
   __shared__ Stage sStage[kF32Warps][kStages];  // the batch's matching lambda blocks
@@ -611,12 +618,300 @@ __global__ void __launch_bounds__(kDfWarps * 32, 3) mul_df_kernel(MulArgs a, con
   }
 }
 
+// Split-bfloat16 tensor-core product (S_BF16X3): float operands pre-split into three
+// bfloat16 planes, a = a0 + a1 + a2 to 2^-24 relative; the six leading cross products
+// a_i b_j (i + j <= 2, smallest first) run on the tensor cores as m16n8k8 bf16 MMAs with
+// float accumulation, per lambda block, and the lambda sum is compensated as in the float
+// kernel.  Output tiles of 20 x 20 padded to 32 x 24 (two m16, three n8), lambda slices of 20
+// padded to 24 (three k8).  Staging: 4- or 8-byte cp.async copies of the planes into
+// double-buffered shared tiles, op(X) as [k][m] (80-byte rows) or [m][k] (48-byte rows),
+// op(Y) as [k][n] (80-byte rows), all read by ldmatrix (.trans where k is the row).
+__global__ void split3_kernel(int64_t n, const float* __restrict__ a, __nv_bfloat16* __restrict__ p0,
+                              __nv_bfloat16* __restrict__ p1, __nv_bfloat16* __restrict__ p2) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const float v = a[i];
+    const __nv_bfloat16 h0 = __float2bfloat16_rn(v);
+    const float r1 = v - __bfloat162float(h0);
+    const __nv_bfloat16 h1 = __float2bfloat16_rn(r1);
+    const float r2 = r1 - __bfloat162float(h1);
+    p0[i] = h0;
+    p1[i] = h1;
+    p2[i] = __float2bfloat16_rn(r2);
+  }
+}
+
+constexpr int kTcWarps = 4;
+constexpr int kTcK = 24;        // padded lambda slice (three k8)
+constexpr int kTcLdKM = 40;     // [k][m] and [k][n] row length in bf16 (80 bytes)
+constexpr int kTcLdMK = 24;     // [m][k] row length in bf16 (48 bytes)
+constexpr int kTcPlane = 32 * kTcLdKM;  // bf16 per operand plane per buffer (covers both layouts)
+// per warp: [buf 2][operand 2][plane 3][kTcPlane]
+constexpr size_t kTcSmem = sizeof(__nv_bfloat16) * kTcWarps * 2 * 2 * 3 * kTcPlane;
+
+__device__ __forceinline__ void cp_async_b(void* dst, const void* src, int bytes) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  if (bytes == 8) asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(d), "l"(src));
+  else asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(d), "l"(src));
+}
+
+struct Planes {
+  const __nv_bfloat16* p[3];
+};
+
+// Copy one lambda slice of op(X) and op(Y) (three planes each) into the stage buffer.
+template <bool TX, bool TY>
+__device__ __forceinline__ void tc_stage_copy(const Stage& sg, const Planes& X, const Planes& Y, const int64_t* xvoff,
+                                              const int64_t* yvoff, int ni, int nj, int r0, int c0, int th, int tw,
+                                              int lane, __nv_bfloat16* xs, __nv_bfloat16* ys) {
+  const int nl = sg.nl, t0 = sg.t0;
+  const int tk = min(kTile, nl - t0);
+  const int64_t xo = xvoff[sg.bx], yo = yvoff[sg.by];
+  // op(X): TX -> stored (lambda, nu) rows t: [k][m] layout, a run of th along m per k
+  //        !TX -> stored (nu, lambda) rows r: [m][k] layout, a run of tk along k per m
+  const int xrun = TX ? th : tk, xrows = TX ? tk : th;
+  // bf16 per copy: 4 (8 bytes) when row length, run start and run length are multiples of
+  // 4, else 2 (4 bytes; all block sizes and tile offsets are even, block offsets are
+  // multiples of 4 entries since they are sums of products of even sizes)
+  const int xch = (((TX ? (ni | r0 | th) : (nl | t0 | tk)) & 3) == 0) ? 4 : 2;
+  const int xper = xrun / xch;
+  const float rxp = 1.0f / (float)xper;
+  for (int e = lane; e < xrows * xper; e += 32) {
+    const int row = __float2int_rz(((float)e + 0.5f) * rxp), q = e - row * xper;
+    const int64_t src = TX ? xo + (int64_t)(t0 + row) * ni + r0 + q * xch : xo + (int64_t)(r0 + row) * nl + t0 + q * xch;
+    __nv_bfloat16* dst = xs + (TX ? row * kTcLdKM : row * kTcLdMK) + q * xch;
+#pragma unroll
+    for (int pl = 0; pl < 3; ++pl) cp_async_b(dst + pl * kTcPlane, X.p[pl] + src, xch * 2);
+  }
+  // op(Y): !TY -> stored (lambda, nu') rows t: [k][n], a run of tw along n per k
+  const int ych = ((nj | c0 | tw) & 3) == 0 ? 4 : 2;
+  const int yper = tw / ych;
+  if (!TY) {
+    const float ryp = 1.0f / (float)yper;
+    for (int e = lane; e < tk * yper; e += 32) {
+      const int row = __float2int_rz(((float)e + 0.5f) * ryp), q = e - row * yper;
+      const int64_t src = yo + (int64_t)(t0 + row) * nj + c0 + q * ych;
+#pragma unroll
+      for (int pl = 0; pl < 3; ++pl)
+        cp_async_b(ys + pl * kTcPlane + row * kTcLdKM + q * ych, Y.p[pl] + src, ych * 2);
+    }
+  } else {
+    // TY: stored (nu', lambda): element (t, c) at c * nl + t; scalar copies
+    const float rtw = 1.0f / (float)tw;
+    for (int e = lane; e < tk * tw; e += 32) {
+      const int row = __float2int_rz(((float)e + 0.5f) * rtw), c = e - row * tw;
+#pragma unroll
+      for (int pl = 0; pl < 3; ++pl)
+        ys[pl * kTcPlane + row * kTcLdKM + c] = Y.p[pl][yo + (int64_t)(c0 + c) * nl + t0 + row];
+    }
+  }
+}
+
+__device__ __forceinline__ void ldsm_x2(unsigned& r0, unsigned& r1, const void* p) {
+  const unsigned a = (unsigned)__cvta_generic_to_shared(p);
+  asm volatile("ldmatrix.sync.aligned.m8n8.x2.shared.b16 {%0,%1}, [%2];\n" : "=r"(r0), "=r"(r1) : "r"(a));
+}
+__device__ __forceinline__ void ldsm_x2_t(unsigned& r0, unsigned& r1, const void* p) {
+  const unsigned a = (unsigned)__cvta_generic_to_shared(p);
+  asm volatile("ldmatrix.sync.aligned.m8n8.x2.trans.shared.b16 {%0,%1}, [%2];\n" : "=r"(r0), "=r"(r1) : "r"(a));
+}
+__device__ __forceinline__ void ldsm_x1_t(unsigned& r0, const void* p) {
+  const unsigned a = (unsigned)__cvta_generic_to_shared(p);
+  asm volatile("ldmatrix.sync.aligned.m8n8.x1.trans.shared.b16 {%0}, [%1];\n" : "=r"(r0) : "r"(a));
+}
+__device__ __forceinline__ void mma_bf16_k8(float* c, unsigned a0, unsigned a1, unsigned b0) {
+  asm volatile("mma.sync.aligned.m16n8k8.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5}, {%6}, {%0,%1,%2,%3};\n"
+               : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+               : "r"(a0), "r"(a1), "r"(b0));
+}
+
+template <bool TX, bool TY>
+__global__ void __launch_bounds__(kTcWarps * 32, 2) mul_bf16x3_kernel(MulArgs a, Planes X, Planes Y,
+                                                                      float* __restrict__ C) {
+  extern __shared__ __align__(16) __nv_bfloat16 tsm[];
+  __shared__ Stage sStage[kTcWarps][kStages];
+  const int lane = threadIdx.x & 31;
+  const int w = threadIdx.x >> 5;
+  __nv_bfloat16* base = tsm + (size_t)w * 2 * 2 * 3 * kTcPlane;  // [buf][X|Y][plane][kTcPlane]
+  Stage* st = sStage[w];
+  // zero the warp's buffers once: padding rows/columns stay zero
+  for (int e = lane; e < 2 * 2 * 3 * kTcPlane / 2; e += 32) reinterpret_cast<unsigned*>(base)[e] = 0u;
+  __syncwarp();
+  const int g = lane >> 2, tq = lane & 3;
+  // ldmatrix row addresses: lanes 0-7 give rows of matrix 0, 8-15 of matrix 1
+  const int lr = lane & 7, lm = (lane >> 3) & 1;
+  for (;;) {
+    unsigned int t = 0;
+    if (lane == 0) t = atomicAdd(a.counter, 1u);
+    t = __shfl_sync(0xffffffffu, t, 0);
+    if (t >= a.ntiles) break;
+    const Tile tile = a.tiles[t];
+    const int k = tile.blk;
+    const int nu = a.c_brow[k], nup = a.c_col[k];
+    const int ni = a.bsize[nu], nj = a.bsize[nup];
+    const int th = min(kTile, ni - tile.r0), tw = min(kTile, nj - tile.c0);
+    float pc[2][3][4], acc[2][3][4], comp[2][3][4];
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+#pragma unroll
+      for (int j = 0; j < 3; ++j)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) pc[i][j][q] = acc[i][j][q] = comp[i][j][q] = 0.0f;
+    int folded = 0;
+    int tk_b0 = kTile, tk_b1 = kTile;  // width of the slice last copied into each buffer
+    const int px1 = (int)a.x.ptr[nu + 1];
+    int px = (int)a.x.ptr[nu];
+    int py0 = (int)a.y.ptr[nup];
+    const int py1 = (int)a.y.ptr[nup + 1];
+    while (px < px1 && py0 < py1) {
+      int nm = 0;
+      while (px < px1 && py0 < py1 && nm <= kStages - 32) {
+        const int i = px + lane;
+        const int32_t lam = i < px1 ? __ldg(a.x.idx + i) : INT32_MAX;
+        const int pos = lower_bound_dev(a.y.idx, py0, py1, lam);
+        const bool hit = i < px1 && pos < py1 && __ldg(a.y.idx + pos) == lam;
+        const unsigned int mask = __ballot_sync(0xffffffffu, hit);
+        if (hit) {
+          const int kx = a.x.blk ? __ldg(a.x.blk + i) : i;
+          const int ky = a.y.blk ? __ldg(a.y.blk + pos) : pos;
+          st[nm + __popc(mask & ((1u << lane) - 1u))] = Stage{kx, ky, (int16_t)a.bsize[lam], 0};
+        }
+        nm += __popc(mask);
+        py0 = __shfl_sync(0xffffffffu, pos, 31);
+        px += 32;
+      }
+      __syncwarp();
+      if (nm == 0) continue;
+      int m = 0, q = 0, buf = 0;
+      // slices narrower than an earlier one in the same buffer leave stale k rows/columns:
+      // zero them before copying (K padding must be zero in both operands)
+      auto prep = [&](int b, int tk) {
+        if (tk < (b ? tk_b1 : tk_b0)) {
+          __nv_bfloat16* xb = base + (b * 2 + 0) * 3 * kTcPlane;
+          __nv_bfloat16* yb = base + (b * 2 + 1) * 3 * kTcPlane;
+          const __nv_bfloat16 z = __float2bfloat16_rn(0.0f);
+          for (int kk = tk; kk < kTile; ++kk)      // lane = m (or n) index
+#pragma unroll
+            for (int pl = 0; pl < 3; ++pl) {
+              if (TX) xb[pl * kTcPlane + kk * kTcLdKM + lane] = z;
+              else if (lane < kTcLdMK) xb[pl * kTcPlane + lane * kTcLdMK + kk] = z;
+              yb[pl * kTcPlane + kk * kTcLdKM + lane] = z;
+            }
+        }
+        if (b) tk_b1 = tk;
+        else tk_b0 = tk;
+      };
+      {
+        const int tk0 = min(kTile, (int)st[0].nl);
+        prep(0, tk0);
+        __syncwarp();
+        tc_stage_copy<TX, TY>(st[0], X, Y, a.x.voff, a.y.voff, ni, nj, tile.r0, tile.c0, th, tw, lane,
+                              base, base + 3 * kTcPlane);
+        cp_commit();
+      }
+      for (;;) {
+        const Stage cur = st[m];
+        const int t0 = q * kTile;
+        const bool last_slice = t0 + kTile >= (int)cur.nl;
+        const int nm2 = last_slice ? m + 1 : m, nq2 = last_slice ? 0 : q + 1;
+        const bool more = nm2 < nm;
+        if (more) {
+          Stage sg = st[nm2];
+          sg.t0 = (int16_t)(nq2 * kTile);
+          prep(buf ^ 1, min(kTile, (int)sg.nl - (int)sg.t0));
+          __syncwarp();
+          __nv_bfloat16* nb = base + (buf ^ 1) * 2 * 3 * kTcPlane;
+          tc_stage_copy<TX, TY>(sg, X, Y, a.x.voff, a.y.voff, ni, nj, tile.r0, tile.c0, th, tw, lane, nb,
+                                nb + 3 * kTcPlane);
+          cp_commit();
+          cp_wait<1>();
+        } else {
+          cp_wait<0>();
+        }
+        __syncwarp();
+        {
+          const __nv_bfloat16* xs = base + buf * 2 * 3 * kTcPlane;
+          const __nv_bfloat16* ys = xs + 3 * kTcPlane;
+#pragma unroll
+          for (int kk = 0; kk < 3; ++kk) {
+            // fragments of the three planes for this k8 step
+            unsigned af[3][2][2], bfr[3][3];
+#pragma unroll
+            for (int pl = 0; pl < 3; ++pl) {
+#pragma unroll
+              for (int mi = 0; mi < 2; ++mi) {
+                if (TX) {
+                  // [k][m]: matrix 0 = m 0-7, matrix 1 = m 8-15 of this m16, rows k
+                  const __nv_bfloat16* pa = xs + pl * kTcPlane + (kk * 8 + lr) * kTcLdKM + mi * 16 + lm * 8;
+                  ldsm_x2_t(af[pl][mi][0], af[pl][mi][1], pa);
+                } else {
+                  const __nv_bfloat16* pa = xs + pl * kTcPlane + (mi * 16 + lm * 8 + lr) * kTcLdMK + kk * 8;
+                  ldsm_x2(af[pl][mi][0], af[pl][mi][1], pa);
+                }
+              }
+#pragma unroll
+              for (int nj8 = 0; nj8 < 3; ++nj8) {
+                const __nv_bfloat16* pb = ys + pl * kTcPlane + (kk * 8 + lr) * kTcLdKM + nj8 * 8;
+                ldsm_x1_t(bfr[pl][nj8], pb);
+              }
+            }
+#pragma unroll
+            for (int mi = 0; mi < 2; ++mi)
+#pragma unroll
+              for (int nj8 = 0; nj8 < 3; ++nj8) {
+                float* c = pc[mi][nj8];
+                mma_bf16_k8(c, af[2][mi][0], af[2][mi][1], bfr[0][nj8]);
+                mma_bf16_k8(c, af[1][mi][0], af[1][mi][1], bfr[1][nj8]);
+                mma_bf16_k8(c, af[0][mi][0], af[0][mi][1], bfr[2][nj8]);
+                mma_bf16_k8(c, af[1][mi][0], af[1][mi][1], bfr[0][nj8]);
+                mma_bf16_k8(c, af[0][mi][0], af[0][mi][1], bfr[1][nj8]);
+                mma_bf16_k8(c, af[0][mi][0], af[0][mi][1], bfr[0][nj8]);
+              }
+          }
+        }
+        __syncwarp();
+        if (last_slice && ++folded == kFold) {
+          folded = 0;
+#pragma unroll
+          for (int i = 0; i < 2; ++i)
+#pragma unroll
+            for (int j = 0; j < 3; ++j)
+#pragma unroll
+              for (int qq = 0; qq < 4; ++qq) {
+                const float hi = acc[i][j][qq] + pc[i][j][qq];
+                const float bp = hi - acc[i][j][qq];
+                comp[i][j][qq] += (acc[i][j][qq] - (hi - bp)) + (pc[i][j][qq] - bp);
+                acc[i][j][qq] = hi;
+                pc[i][j][qq] = 0.0f;
+              }
+        }
+        if (!more) break;
+        m = nm2;
+        q = nq2;
+        buf ^= 1;
+      }
+    }
+    float* cb = C + a.c_voff[k];
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+#pragma unroll
+      for (int j = 0; j < 3; ++j)
+#pragma unroll
+        for (int qq = 0; qq < 4; ++qq) {
+          const int r = i * 16 + g + (qq >= 2 ? 8 : 0), c = j * 8 + 2 * tq + (qq & 1);
+          const float hi = acc[i][j][qq] + pc[i][j][qq];
+          const float bp = hi - acc[i][j][qq];
+          const float err = (acc[i][j][qq] - (hi - bp)) + (pc[i][j][qq] - bp);
+          if (r < th && c < tw) cb[(int64_t)(tile.r0 + r) * nj + tile.c0 + c] = hi + (comp[i][j][qq] + err);
+        }
+  }
+}
+
 // The float kernel variants the autotuner chooses from: tile edge and lane micro-tile.
 struct F32Variant {
   int tt, mr, mc;
 };
-constexpr F32Variant kF32Variants[] = {{20, 4, 4}, {16, 4, 2}, {12, 3, 2}, {8, 2, 1}};
-constexpr int kNumF32Variants = 4;
+constexpr F32Variant kF32Variants[] = {{20, 4, 4}, {16, 4, 2}, {12, 3, 2}, {8, 2, 1}, {10, 2, 2}};
+constexpr int kNumF32Variants = 5;
 
 static int g_sms = 0;
 static int num_sms() {
@@ -718,6 +1013,17 @@ s_status build_desc(const s_pattern_t* X, bool tx, const s_pattern_t* Y, bool ty
   cudaFree(bflops);
   if (e != cudaSuccess) st = cuda_error(e, "s_plan_create(symbolic)");
   if (!st) st = build_tiles(&d, kF32Variants[0].tt);
+  if (!st && prec == S_BF16X3) {
+    // three bfloat16 planes per operand; every block size must be even (4-byte copies)
+    for (const s_pattern_t* q : {X, Y, C})
+      for (int32_t b : q->bsize)
+        if (b & 1) st = set_error(S_ERR_ARG, "S_BF16X3 needs even block sizes");
+    if (!st) {
+      e = cudaMalloc(&d.bf_x, sizeof(__nv_bfloat16) * 3 * std::max<int64_t>(X->d.nnz, 1));
+      if (e == cudaSuccess) e = cudaMalloc(&d.bf_y, sizeof(__nv_bfloat16) * 3 * std::max<int64_t>(Y->d.nnz, 1));
+      if (e != cudaSuccess) st = cuda_error(e, "cudaMalloc(split-bfloat16 scratch)");
+    }
+  }
   if (!st && prec == S_FP64_DF) {
     // split operands (float pairs), reused by every call of this plan
     e = cudaMalloc(&d.df_x, sizeof(float2) * std::max<int64_t>(X->d.nnz, 1));
@@ -738,6 +1044,9 @@ void free_desc(MulDesc* d) {
   cudaFree(d->df_x);
   cudaFree(d->df_y);
   d->df_x = d->df_y = nullptr;
+  cudaFree(d->bf_x);
+  cudaFree(d->bf_y);
+  d->bf_x = d->bf_y = nullptr;
   d->tiles = nullptr;
   d->counter = nullptr;
   d->ntiles = 0;
@@ -754,6 +1063,7 @@ static F32Kernel f32_kernel(bool tx, bool ty) {
 
 static F32Kernel f32_kernel_of(int v, bool tx, bool ty) {
   switch (v) {
+    case 4: return f32_kernel<4>(tx, ty);
     case 1: return f32_kernel<1>(tx, ty);
     case 2: return f32_kernel<2>(tx, ty);
     case 3: return f32_kernel<3>(tx, ty);
@@ -836,6 +1146,45 @@ static s_status launch_df(const MulDesc& d, const void* X, const void* Y, void* 
   return S_OK;
 }
 
+static s_status launch_bf16x3(const MulDesc& d, const void* X, const void* Y, void* C, cudaStream_t st) {
+  if (d.ntiles == 0) return S_OK;
+  if (d.edge != kTile) return set_error(S_ERR_ARG, "internal: split-bfloat16 kernel needs 20-wide tiles");
+  if (!d.bf_x || !d.bf_y) return set_error(S_ERR_ARG, "internal: split-bfloat16 scratch missing");
+  const int64_t nx = d.px->d.nnz, ny = d.py->d.nnz;
+  const int gx = (int)std::max<int64_t>(1, std::min<int64_t>((nx + 255) / 256, (int64_t)num_sms() * 16));
+  const int gy = (int)std::max<int64_t>(1, std::min<int64_t>((ny + 255) / 256, (int64_t)num_sms() * 16));
+  if (nx) split3_kernel<<<gx, 256, 0, st>>>(nx, (const float*)X, d.bf_x, d.bf_x + nx, d.bf_x + 2 * nx);
+  Planes px{{d.bf_x, d.bf_x + nx, d.bf_x + 2 * nx}};
+  Planes py = px;
+  if (Y != X || d.px != d.py) {
+    if (ny) split3_kernel<<<gy, 256, 0, st>>>(ny, (const float*)Y, d.bf_y, d.bf_y + ny, d.bf_y + 2 * ny);
+    py = Planes{{d.bf_y, d.bf_y + ny, d.bf_y + 2 * ny}};
+  }
+  MulArgs a;
+  a.x = dev_side(d.x);
+  a.y = dev_side(d.y);
+  a.bsize = d.pc->d.bsize;
+  a.c_brow = d.pc->d.brow;
+  a.c_col = d.pc->d.colidx;
+  a.c_voff = d.pc->d.voff;
+  a.tiles = d.tiles;
+  a.ntiles = d.ntiles;
+  a.counter = d.counter;
+  SF_CUDA(cudaMemsetAsync(d.counter, 0, sizeof(unsigned int), st));
+  using K = void (*)(MulArgs, Planes, Planes, float*);
+  K kern = d.x.trans ? (d.y.trans ? mul_bf16x3_kernel<true, true> : mul_bf16x3_kernel<true, false>)
+                     : (d.y.trans ? mul_bf16x3_kernel<false, true> : mul_bf16x3_kernel<false, false>);
+  SF_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTcSmem));
+  int per_sm = 0;
+  SF_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kTcWarps * 32, kTcSmem));
+  if (per_sm < 1) per_sm = 1;
+  const int64_t want = (d.ntiles + kTcWarps - 1) / kTcWarps;
+  const int grid = (int)std::min<int64_t>(want, (int64_t)num_sms() * per_sm);
+  kern<<<grid, kTcWarps * 32, kTcSmem, st>>>(a, px, py, (float*)C);
+  SF_CUDA(cudaGetLastError());
+  return S_OK;
+}
+
 s_status run_mul(const MulDesc& d, s_prec prec, const void* X, const void* Y, void* C, cudaStream_t st) {
   switch (prec) {
     case S_FP64:
@@ -844,6 +1193,8 @@ s_status run_mul(const MulDesc& d, s_prec prec, const void* X, const void* Y, vo
       return launch_typed<float>(d, X, Y, C, st);
     case S_FP64_DF:
       return launch_df(d, X, Y, C, st);
+    case S_BF16X3:
+      return launch_bf16x3(d, X, Y, C, st);
     default:
       return set_error(S_ERR_ARG, "precision not supported by this product path");
   }
@@ -863,8 +1214,8 @@ extern "C" s_status s_plan_create(s_pattern A, s_pattern B, s_pattern C, s_prec 
   if (!out) return set_error(S_ERR_ARG, "s_plan_create: out is NULL");
   *out = nullptr;
   if (!A || !B || !C) return set_error(S_ERR_ARG, "s_plan_create: NULL pattern");
-  if (prec != S_FP64 && prec != S_FP32 && prec != S_FP64_DF)
-    return set_error(S_ERR_ARG, "s_plan_create: unsupported precision (S_FP64, S_FP32 or S_FP64_DF)");
+  if (prec != S_FP64 && prec != S_FP32 && prec != S_FP64_DF && prec != S_BF16X3)
+    return set_error(S_ERR_ARG, "s_plan_create: unsupported precision");
   s_status st;
   if ((st = check_same_tree(A, B)) || (st = check_same_tree(A, C))) return st;
   s_plan_t* p = new (std::nothrow) s_plan_t();

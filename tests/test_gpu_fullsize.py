@@ -1,11 +1,14 @@
 """Parity at the benchmark's full size (N = 2^20 points in [0,1]^3, Matern-1/2, ell = 0.1,
 q = 3, leaf 32, eta = 1.0, tau = 1e-8), in the launch configuration bench.py times: the
-FP64 and mixed products of the whole pattern on the GPU, compared on a seeded sample of
+FP64, mixed (compensated float) and split-bfloat16 tensor-core products of the whole pattern on the GPU, compared on a seeded sample of
 output blocks that the FP64 oracle computes one by one (plus every block of the root's row,
 whose lambda lists are the longest, and the last block).
 
-Tolerances as for the small cases: FP64 within 1e-12 relative Frobenius over the sampled
-blocks, mixed (compensated float) within 1e-6."""
+Tolerances: FP64 within 1e-12 relative Frobenius over the sampled blocks, mixed
+(compensated float) within 1e-6, split-bfloat16 tensor-core products within 5e-6: the
+tensor cores' float accumulation over the 18 k8 steps of a lambda slice loses about 2^-23
+per step (measured 2.2e-6 over the whole product), above the 1e-6 the compensated float
+kernel reaches."""
 import os
 
 import numpy as np
@@ -31,14 +34,18 @@ def c2():
     p32 = sf.Plan(pat, pat, pat, "fp32")
     p32.set_symmetric_a(True)          # as bench.py: A = T K T^T is symmetric
     p32.mul(A32, A32, C32)
+    Cb = torch.empty_like(A32)
+    pb = sf.Plan(pat, pat, pat, "bf16x3")
+    pb.set_symmetric_a(True)
+    pb.mul(A32, A32, Cb)
     torch.cuda.synchronize()
-    return pat, vals.cpu().numpy(), C64.cpu().numpy(), C32.double().cpu().numpy()
+    return pat, vals.cpu().numpy(), C64.cpu().numpy(), C32.double().cpu().numpy(), Cb.double().cpu().numpy()
 
 
 def test_fullsize_sampled_parity(c2):
     from oracle import product as oprod
     from oracle.sformat import BlockCSR
-    pat, aval, c64, c32 = c2
+    pat, aval, c64, c32, cb = c2
     bo, rp, ci = pat.arrays()
     A = BlockCSR(np.diff(bo), rp, ci.astype(np.int64), aval)
     rng = np.random.Generator(np.random.PCG64(2024))
@@ -50,3 +57,4 @@ def test_fullsize_sampled_parity(c2):
     n = np.linalg.norm(want)
     assert np.linalg.norm(c64[idx] - want) <= 1e-12 * n
     assert np.linalg.norm(c32[idx] - want) <= 1e-6 * n
+    assert np.linalg.norm(cb[idx] - want) <= 5e-6 * n

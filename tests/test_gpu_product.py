@@ -106,6 +106,38 @@ def test_general_patterns_and_ragged_tiles(sf, seed):
     assert rel_frob(host(hB), wB.val) <= 1e-12
 
 
+@pytest.mark.parametrize("seed", [5, 6])
+def test_bf16x3_general_even_patterns(sf, seed):
+    # even block sizes up to 44 (tiles and lambda slices with ragged ends, 4- and 8-byte copies);
+    # uniform [-1, 1] values cancel about tenfold in these sums, so the float-class bound
+    # of the random-pattern tests (1e-5) applies, as for the compensated float kernel
+    rng = np.random.Generator(np.random.PCG64(seed))
+    bsize = 2 * rng.integers(0, 23, size=28)
+    A = drop_empty(random_bcsr(bsize, 0.35, seed * 10))
+    B = drop_empty(random_bcsr(bsize, 0.35, seed * 20, diag=False))
+    Cp = drop_empty(random_bcsr(bsize, 0.4, seed * 30, diag=False))
+    want = oprod.mul_masked(A, B, Cp).val
+    pa, pb, pc = pattern_of(A), pattern_of(B), pattern_of(Cp)
+    plan = sf.Plan(pa, pb, pc, "bf16x3")
+    out = dev(np.full(len(Cp.val), np.nan), "float32")
+    plan.mul(dev(A.val, "float32"), dev(B.val, "float32"), out)
+    assert rel_frob(host(out), want) <= 1e-5
+    dC = Cp.like(W.random_values(len(Cp.val), seed + 7))
+    gA, gB = dev(np.zeros(len(A.val)), "float32"), dev(np.zeros(len(B.val)), "float32")
+    plan.adjoint(dev(dC.val, "float32"), dev(A.val, "float32"), dev(B.val, "float32"), gA, gB)
+    wA, wB = oadj.mul_masked_adjoint(dC, A, B)
+    assert rel_frob(host(gA), wA.val) <= 1e-5
+    assert rel_frob(host(gB), wB.val) <= 1e-5
+
+
+def test_bf16x3_rejects_odd_blocks(sf):
+    A = random_bcsr(np.array([3, 4, 6]), 1.0, 3)
+    p = pattern_of(A)
+    with pytest.raises(sf.SFormatError) as e:
+        sf.Plan(p, p, p, "bf16x3")
+    assert e.value.status == sf.S_ERR_ARG
+
+
 def drop_empty(X):
     from oracle.sformat import BlockCSR
     keep_rows, cols = [0], []
@@ -126,6 +158,14 @@ def test_c1_fp32_error_and_add(sf, c1):
     c, levels = c1
     A = c.A
     P = pattern_of(A, levels)
+    # split-bfloat16 tensor-core product (six cross products of three bf16 planes)
+    want0 = oprod.mul_masked(A, A, A, nthreads=8).val
+    for sym in (False, True):
+        pb = sf.Plan(P, P, P, "bf16x3")
+        pb.set_symmetric_a(sym)
+        ob = dev(np.full(len(A.val), np.nan), "float32")
+        pb.mul(dev(A.val, "float32"), dev(A.val, "float32"), ob)
+        assert rel_frob(host(ob), want0) <= 1e-6
     plan = sf.Plan(P, P, P, "fp32")
     out = dev(np.zeros(len(A.val)), "float32")
     plan.mul(dev(A.val, "float32"), dev(A.val, "float32"), out)
