@@ -385,6 +385,9 @@ def main():
     A32 = vals.float()
     C32 = torch.empty_like(A32)
     stream = torch.cuda.current_stream()
+    t0 = time.time()
+    shape = plan32.autotune(A32, A32, C32)      # kernel shape for this pattern
+    prep["autotune_s"] = round(time.time() - t0, 2)
     for _ in range(args.warmup):
         plan32.mul(A32, A32, C32)
     torch.cuda.synchronize()
@@ -504,8 +507,8 @@ def main():
         "fp64": fp64,
         "roofline": {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
                      "frac": achieved / fp32_peak, "traffic": kernel_traffic(),
-                     "kernel": "sf::mul_f32_kernel<%d,%d,%d,true,false>" % (
-                         plan32.variant()["tile"], *plan32.variant()["micro"]),
+                     "kernel": "sf::mul_f32_kernel<tile %d, micro %dx%d, transposed A>" % (
+                         shape["tile"], *shape["micro"]),
                      "peak_source": "152 SMs x 128 FP32 lanes x 2 flop x sm_max_mhz (derived)"},
         "clocks": clocks,
         "e2e": e2e,

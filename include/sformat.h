@@ -105,8 +105,8 @@ s_status s_plan_create(s_pattern A, s_pattern B, s_pattern C, s_prec prec, s_pla
 s_status s_plan_destroy(s_plan plan);
 /* Exact triple count and useful flop count of the plan's product. */
 s_status s_plan_stats(s_plan plan, int64_t* triples, double* flops);
-/* Autotuner of S_FP32 plans: times every float kernel variant (output tile edge and the
- * micro-tile of one lane) on the given operands, three launches each after one warm-up,
+/* Autotuner of S_FP32 plans: times every float kernel variant (output tile edge, the
+ * micro-tile of one lane, the lambda extent of a stage) on the given operands, three launches each after one warm-up,
  * and keeps the fastest for this plan's forward product.  C is overwritten.  *chosen
  * (optional) receives the variant index.  S_FP64 plans have one shape (no-op).
  * Synchronises the stream. */
@@ -121,8 +121,10 @@ int s_plan_num_variants(void);
  * Checks that A's pattern is symmetric (S_ERR_PATTERN otherwise); the values are the
  * caller's promise.  symmetric = 0 restores the default. */
 s_status s_plan_set_symmetric_a(s_plan plan, int symmetric);
-/* Shape of a float variant (variant < 0: the plan's current one): tile edge and micro-tile. */
-s_status s_plan_variant(s_plan plan, int variant, int* tile, int* micro_rows, int* micro_cols);
+/* Shape of a float variant (variant < 0: the plan's current one): output tile edge, the
+ * micro-tile of one lane, and the largest lambda extent staged at once (consecutive small
+ * lambda blocks are packed into one stage up to this extent).  Any output may be NULL. */
+s_status s_plan_variant(s_plan plan, int variant, int* tile, int* micro_rows, int* micro_cols, int* stage_k);
 
 /* C = P_{S_C}(A B): for every block (nu, nu') of S_C,
  *   C(nu, nu') = sum over lambda with (nu,lambda) in S_A and (lambda,nu') in S_B of

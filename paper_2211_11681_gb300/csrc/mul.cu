@@ -255,29 +255,33 @@ __device__ __forceinline__ void lds(const float* p, float* out) {
   }
 }
 
+// Copies lambda slice [t0, t0 + wd) of op(X) rows r0.. (th of them) and op(Y) columns
+// c0.. (tw of them) into rows k0 .. k0 + wd - 1 of the stage buffers: xs[k][r], ys[k][c].
 template <int TT, bool TX, bool TY>
-__device__ __forceinline__ void stage_copy(const Stage& sg, const float* __restrict__ X, const float* __restrict__ Y,
-                                           const int64_t* xvoff, const int64_t* yvoff, int ni, int nj, int r0,
-                                           int c0, int th, int tw, int lane, float* xs, float* ys) {
-  const int nl = sg.nl, t0 = sg.t0;
-  const int tk = min(TT, nl - t0);
+__device__ __forceinline__ void stage_copy(const Stage& sg, int t0, int wd, int k0, const float* __restrict__ X,
+                                           const float* __restrict__ Y, const int64_t* xvoff, const int64_t* yvoff,
+                                           int ni, int nj, int r0, int c0, int th, int tw, int lane, float* xs,
+                                           float* ys) {
+  const int nl = sg.nl;
   const float* xb = X + xvoff[sg.bx];
   const float* yb = Y + yvoff[sg.by];
-  const float rtk = 1.0f / (float)tk;
+  xs += k0 * TT;
+  ys += k0 * TT;
   const bool xvec = TT % 4 == 0 && TX && r0 == 0 && th == ni && (ni & 3) == 0 &&
                     ((reinterpret_cast<uintptr_t>(xb) & 15) == 0);
   if (xvec) {
     // op(X) = X^T: row t of the stored block (lambda, nu) is column t of op(X), i.e. one
-    // contiguous run of sA[t][.]
+    // contiguous run of xs[t][.]
     const float rni = 1.0f / (float)ni;
-    for (int q = lane; q < (tk * ni) >> 2; q += 32) {
+    for (int q = lane; q < (wd * ni) >> 2; q += 32) {
       const int e = q << 2;
       const int tt = __float2int_rz(((float)e + 0.5f) * rni), r = e - tt * ni;
       cp_async16(xs + tt * TT + r, xb + (int64_t)(t0 + tt) * ni + r);
     }
   } else {
-    for (int e = lane; e < th * tk; e += 32) {
-      const int r = __float2int_rz(((float)e + 0.5f) * rtk), tt = e - r * tk;
+    const float rwd = 1.0f / (float)wd;
+    for (int e = lane; e < th * wd; e += 32) {
+      const int r = __float2int_rz(((float)e + 0.5f) * rwd), tt = e - r * wd;
       const int gr = r0 + r, gt = t0 + tt;
       cp_async4(xs + tt * TT + r, TX ? xb + (int64_t)gt * ni + gr : xb + (int64_t)gr * nl + gt);
     }
@@ -287,14 +291,14 @@ __device__ __forceinline__ void stage_copy(const Stage& sg, const float* __restr
                    ((reinterpret_cast<uintptr_t>(yb) & 15) == 0);
   if (vec) {
     const float rnj = 1.0f / (float)nj;
-    for (int q = lane; q < (tk * nj) >> 2; q += 32) {
+    for (int q = lane; q < (wd * nj) >> 2; q += 32) {
       const int e = q << 2;
       const int tt = __float2int_rz(((float)e + 0.5f) * rnj), c = e - tt * nj;
       cp_async16(ys + tt * TT + c, yb + (int64_t)(t0 + tt) * nj + c);
     }
   } else {
     const float rtw = 1.0f / (float)tw;
-    for (int e = lane; e < tk * tw; e += 32) {
+    for (int e = lane; e < wd * tw; e += 32) {
       const int tt = __float2int_rz(((float)e + 0.5f) * rtw), c = e - tt * tw;
       const int gt = t0 + tt, gc = c0 + c;
       cp_async4(ys + tt * TT + c, TY ? yb + (int64_t)gc * nl + gt : yb + (int64_t)gt * nj + gc);
@@ -302,19 +306,66 @@ __device__ __forceinline__ void stage_copy(const Stage& sg, const float* __restr
   }
 }
 
-template <int TT, int MR, int MC, bool TX, bool TY>
+// A pack: the lambda work of one stage, either whole consecutive lambda blocks [m0, m1)
+// whose widths add up to at most KM, or one KM-wide slice [t0, t0 + K) of a block wider
+// than KM.  All lanes compute the same packs.
+struct Pack {
+  int m0, m1, t0, K, done;  // done: lambda blocks completed by this pack
+};
+
+template <int KM>
+__device__ __forceinline__ Pack next_pack(const Stage* st, int nm, int m, int t0) {
+  Pack pk;
+  pk.m0 = m;
+  pk.t0 = t0;
+  const int nl = st[m].nl;
+  if (nl > KM) {
+    pk.K = min(KM, nl - t0);
+    pk.m1 = m + 1;
+    pk.done = (t0 + pk.K >= nl) ? 1 : 0;
+    return pk;
+  }
+  int k = 0, m1 = m;
+  while (m1 < nm && st[m1].nl <= KM && k + st[m1].nl <= KM) {
+    k += st[m1].nl;
+    ++m1;
+  }
+  pk.m1 = m1;
+  pk.K = k;
+  pk.done = m1 - m;
+  return pk;
+}
+
+template <int TT, int KM, bool TX, bool TY>
+__device__ __forceinline__ void pack_copy(const Pack& pk, const Stage* st, const float* __restrict__ X,
+                                          const float* __restrict__ Y, const int64_t* xvoff, const int64_t* yvoff,
+                                          int ni, int nj, int r0, int c0, int th, int tw, int lane, float* xs,
+                                          float* ys) {
+  if (st[pk.m0].nl > KM) {
+    stage_copy<TT, TX, TY>(st[pk.m0], pk.t0, pk.K, 0, X, Y, xvoff, yvoff, ni, nj, r0, c0, th, tw, lane, xs, ys);
+    return;
+  }
+  int k0 = 0;
+  for (int j = pk.m0; j < pk.m1; ++j) {
+    const int nl = st[j].nl;
+    stage_copy<TT, TX, TY>(st[j], 0, nl, k0, X, Y, xvoff, yvoff, ni, nj, r0, c0, th, tw, lane, xs, ys);
+    k0 += nl;
+  }
+}
+
+template <int TT, int MR, int MC, int KM, bool TX, bool TY>
 __global__ void __launch_bounds__(kF32Warps * 32, 4) mul_f32_kernel(MulArgs a, const float* __restrict__ X,
                                                                     const float* __restrict__ Y,
                                                                     float* __restrict__ C) {
   constexpr int GR = TT / MR, GC = TT / MC, NA = GR * GC, NQ = MR * MC;
   static_assert(TT % MR == 0 && TT % MC == 0 && NA <= 32 && TT % 2 == 0 && (MR != 4 || TT % 4 == 0) &&
-                    (MC != 4 || TT % 4 == 0),
+                    (MC != 4 || TT % 4 == 0) && KM >= TT,
                 "bad micro-tile");
-  __shared__ __align__(16) float sA[kF32Warps][2][TT * TT];
-  __shared__ __align__(16) float sB[kF32Warps][2][TT * TT];
+  extern __shared__ __align__(16) float fsm[];   // [warp][buf][A | B][KM * TT]
   __shared__ Stage sStage[kF32Warps][kStages];  // the batch's matching lambda blocks
   const int lane = threadIdx.x & 31;
   const int w = threadIdx.x >> 5;
+  float* wbase = fsm + (size_t)w * 4 * KM * TT;
   Stage* st = sStage[w];
   const bool active = lane < NA;
   const int mr = active ? lane / GC : 0, mc = active ? lane % GC : 0;
@@ -358,34 +409,31 @@ __global__ void __launch_bounds__(kF32Warps * 32, 4) mul_f32_kernel(MulArgs a, c
       }
       __syncwarp();
       if (nm == 0) continue;
-      // ---- stream the slices (lambda block m, slice q): copies of the next slice overlap
-      // the FMAs of the current one
-      int m = 0, q = 0;
-      stage_copy<TT, TX, TY>(st[0], X, Y, a.x.voff, a.y.voff, ni, nj, tile.r0, tile.c0, th, tw, lane, sA[w][0],
-                             sB[w][0]);
+      // ---- stream the packs: the copies of the next pack overlap the FMAs of the current
+      Pack cur = next_pack<KM>(st, nm, 0, 0);
+      pack_copy<TT, KM, TX, TY>(cur, st, X, Y, a.x.voff, a.y.voff, ni, nj, tile.r0, tile.c0, th, tw, lane, wbase,
+                                wbase + KM * TT);
       cp_commit();
       int buf = 0;
       for (;;) {
-        const Stage cur = st[m];
-        const int t0 = q * TT;
-        const bool last_slice = t0 + TT >= (int)cur.nl;
-        const int nm2 = last_slice ? m + 1 : m, nq2 = last_slice ? 0 : q + 1;
-        const bool more = nm2 < nm;
+        const int nm_next = cur.done ? cur.m1 : cur.m0;
+        const int nt_next = cur.done ? 0 : cur.t0 + cur.K;
+        const bool more = nm_next < nm;
+        Pack nxt;
         if (more) {
-          Stage sg = st[nm2];
-          sg.t0 = (int16_t)(nq2 * TT);
-          stage_copy<TT, TX, TY>(sg, X, Y, a.x.voff, a.y.voff, ni, nj, tile.r0, tile.c0, th, tw, lane,
-                                 sA[w][buf ^ 1], sB[w][buf ^ 1]);
+          nxt = next_pack<KM>(st, nm, nm_next, nt_next);
+          float* nb = wbase + (buf ^ 1) * 2 * KM * TT;
+          pack_copy<TT, KM, TX, TY>(nxt, st, X, Y, a.x.voff, a.y.voff, ni, nj, tile.r0, tile.c0, th, tw, lane, nb,
+                                    nb + KM * TT);
           cp_commit();
           cp_wait<1>();
         } else {
           cp_wait<0>();
         }
         __syncwarp();
-        const int tk = min(TT, (int)cur.nl - t0);
         if (active) {
-          const float* xs = sA[w][buf];
-          const float* ys = sB[w][buf];
+          const float* xs = wbase + buf * 2 * KM * TT;
+          const float* ys = xs + KM * TT;
           auto step = [&](int tt) {
             float ar[MR], br[MC];
             lds<MR>(xs + tt * TT + rl, ar);
@@ -395,15 +443,17 @@ __global__ void __launch_bounds__(kF32Warps * 32, 4) mul_f32_kernel(MulArgs a, c
 #pragma unroll
               for (int jj = 0; jj < MC; ++jj) p[ii * MC + jj] = fmaf(ar[ii], br[jj], p[ii * MC + jj]);
           };
-          if (tk == TT) {
+          if (cur.K == KM) {
 #pragma unroll
-            for (int tt = 0; tt < TT; ++tt) step(tt);
+            for (int tt = 0; tt < KM; ++tt) step(tt);
           } else {
-            for (int tt = 0; tt < tk; ++tt) step(tt);
+#pragma unroll 4
+            for (int tt = 0; tt < cur.K; ++tt) step(tt);
           }
         }
         __syncwarp();
-        if (last_slice && ++folded == kFold) {
+        folded += cur.done;
+        if (folded >= kFold) {
           folded = 0;
 #pragma unroll
           for (int qq = 0; qq < NQ; ++qq) {
@@ -415,8 +465,7 @@ __global__ void __launch_bounds__(kF32Warps * 32, 4) mul_f32_kernel(MulArgs a, c
           }
         }
         if (!more) break;
-        m = nm2;
-        q = nq2;
+        cur = nxt;
         buf ^= 1;
       }
     }
@@ -908,10 +957,11 @@ __global__ void __launch_bounds__(kTcWarps * 32, 2) mul_bf16x3_kernel(MulArgs a,
 
 // The float kernel variants the autotuner chooses from: tile edge and lane micro-tile.
 struct F32Variant {
-  int tt, mr, mc;
+  int tt, mr, mc, km;  // tile edge, lane micro-tile, largest lambda extent of one stage
 };
-constexpr F32Variant kF32Variants[] = {{20, 4, 4}, {16, 4, 2}, {12, 3, 2}, {8, 2, 1}, {10, 2, 2}};
-constexpr int kNumF32Variants = 5;
+constexpr F32Variant kF32Variants[] = {{20, 4, 4, 20}, {20, 4, 4, 40}, {16, 4, 2, 32}, {12, 3, 2, 36},
+                                       {10, 2, 2, 40}, {8, 2, 1, 32}};
+constexpr int kNumF32Variants = 6;
 
 static int g_sms = 0;
 static int num_sms() {
@@ -1056,20 +1106,23 @@ using F32Kernel = void (*)(MulArgs, const float*, const float*, float*);
 
 template <int V>
 static F32Kernel f32_kernel(bool tx, bool ty) {
-  constexpr int TT = kF32Variants[V].tt, MR = kF32Variants[V].mr, MC = kF32Variants[V].mc;
-  return tx ? (ty ? mul_f32_kernel<TT, MR, MC, true, true> : mul_f32_kernel<TT, MR, MC, true, false>)
-            : (ty ? mul_f32_kernel<TT, MR, MC, false, true> : mul_f32_kernel<TT, MR, MC, false, false>);
+  constexpr int TT = kF32Variants[V].tt, MR = kF32Variants[V].mr, MC = kF32Variants[V].mc, KM = kF32Variants[V].km;
+  return tx ? (ty ? mul_f32_kernel<TT, MR, MC, KM, true, true> : mul_f32_kernel<TT, MR, MC, KM, true, false>)
+            : (ty ? mul_f32_kernel<TT, MR, MC, KM, false, true> : mul_f32_kernel<TT, MR, MC, KM, false, false>);
 }
 
 static F32Kernel f32_kernel_of(int v, bool tx, bool ty) {
   switch (v) {
-    case 4: return f32_kernel<4>(tx, ty);
     case 1: return f32_kernel<1>(tx, ty);
     case 2: return f32_kernel<2>(tx, ty);
     case 3: return f32_kernel<3>(tx, ty);
+    case 4: return f32_kernel<4>(tx, ty);
+    case 5: return f32_kernel<5>(tx, ty);
     default: return f32_kernel<0>(tx, ty);
   }
 }
+
+static size_t f32_smem(int v) { return sizeof(float) * kF32Warps * 4 * kF32Variants[v].km * kF32Variants[v].tt; }
 
 template <typename T>
 static s_status launch_typed(const MulDesc& d, const void* X, const void* Y, void* C, cudaStream_t st) {
@@ -1089,21 +1142,24 @@ static s_status launch_typed(const MulDesc& d, const void* X, const void* Y, voi
   using K = void (*)(MulArgs, const T*, const T*, T*);
   K kern;
   int warps;
+  size_t dsmem = 0;
   if constexpr (sizeof(T) == 4) {
     if (d.edge != kF32Variants[d.variant].tt) return set_error(S_ERR_ARG, "internal: tile list does not match variant");
     kern = f32_kernel_of(d.variant, d.x.trans, d.y.trans);
     warps = kF32Warps;
+    dsmem = f32_smem(d.variant);
+    SF_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dsmem));
   } else {
     if (d.edge != kTile) return set_error(S_ERR_ARG, "internal: double kernel needs 20-wide tiles");
     kern = d.x.trans ? (d.y.trans ? mul_kernel<T, true, true> : mul_kernel<T, true, false>)
                      : (d.y.trans ? mul_kernel<T, false, true> : mul_kernel<T, false, false>);
     warps = kWarps;
   }
-  SF_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, warps * 32, 0));
+  SF_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, warps * 32, dsmem));
   if (per_sm < 1) per_sm = 1;
   int64_t want = (d.ntiles + warps - 1) / warps;
   int grid = (int)std::min<int64_t>(want, (int64_t)num_sms() * per_sm);
-  kern<<<grid, warps * 32, 0, st>>>(a, (const T*)X, (const T*)Y, (T*)C);
+  kern<<<grid, warps * 32, dsmem, st>>>(a, (const T*)X, (const T*)Y, (T*)C);
   SF_CUDA(cudaGetLastError());
   return S_OK;
 }
@@ -1324,13 +1380,15 @@ extern "C" s_status s_plan_autotune(s_plan p, const void* A, const void* B, void
   return S_OK;
 }
 
-extern "C" s_status s_plan_variant(s_plan p, int variant, int* tile, int* micro_rows, int* micro_cols) {
+extern "C" s_status s_plan_variant(s_plan p, int variant, int* tile, int* micro_rows, int* micro_cols,
+                                   int* stage_k) {
   if (!p) return set_error(S_ERR_ARG, "s_plan_variant: NULL plan");
   if (variant < 0) variant = p->fwd.variant;
   if (variant >= kNumF32Variants) return set_error(S_ERR_ARG, "s_plan_variant: no such variant");
   if (tile) *tile = kF32Variants[variant].tt;
   if (micro_rows) *micro_rows = kF32Variants[variant].mr;
   if (micro_cols) *micro_cols = kF32Variants[variant].mc;
+  if (stage_k) *stage_k = kF32Variants[variant].km;
   return S_OK;
 }
 

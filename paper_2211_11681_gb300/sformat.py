@@ -44,7 +44,7 @@ def _load():
         "s_plan_destroy": (i32, [vp]),
         "s_plan_stats": (i32, [vp, P(i64), P(dbl)]),
         "s_plan_autotune": (i32, [vp, vp, vp, vp, vp, P(i32)]),
-        "s_plan_variant": (i32, [vp, i32, P(i32), P(i32), P(i32)]),
+        "s_plan_variant": (i32, [vp, i32, P(i32), P(i32), P(i32), P(i32)]),
         "s_plan_set_variant": (i32, [vp, i32]),
         "s_plan_set_symmetric_a": (i32, [vp, i32]),
         "s_plan_num_variants": (i32, []),
@@ -193,9 +193,9 @@ class Plan:
         self.variant_index = int(v)
 
     def variant(self):
-        t, r, c = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
-        check(lib.s_plan_variant(self.h, -1, ctypes.byref(t), ctypes.byref(r), ctypes.byref(c)))
-        return {"tile": t.value, "micro": (r.value, c.value)}
+        t, r, c, k = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+        check(lib.s_plan_variant(self.h, -1, ctypes.byref(t), ctypes.byref(r), ctypes.byref(c), ctypes.byref(k)))
+        return {"tile": t.value, "micro": (r.value, c.value), "stage_k": k.value}
 
     def graph(self, A, B, C):
         """CUDA graph of mul(A, B, C) on these buffers."""
