@@ -160,6 +160,20 @@ def measured_peaks():
         return {}
 
 
+def aggregate_ranks(ms, units, dist=None, device="cpu"):
+    """Whole-job throughput of replicas: every rank did `units` of work in its own `ms`; the
+    job time is the slowest rank's (max over ranks), the value is all ranks' units over it
+    (GFLOP/s when units are flops).  Returns (max ms, value)."""
+    world = 1
+    if dist is not None and dist.is_initialized():
+        import torch
+        world = dist.get_world_size()
+        t = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    return ms, units * world / (ms * 1e-3) / 1e9
+
+
 # ---------------------------------------------------------------------------------------
 def oracle_sample(pat, vals_host, cpu_seconds, seed=0):
     """Time the plain-C FP64 oracle on a bounded random sample of output blocks, using all
@@ -416,11 +430,7 @@ def main():
     total_ms = start.elapsed_time(stop)
     launch_ms = [a.elapsed_time(c) for a, c in evs]
     ms = total_ms / args.steps
-    if dist is not None:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    value = flops * world / (ms * 1e-3) / 1e9
+    ms, value = aggregate_ranks(ms, flops, dist, "cuda")
     clocks = clk.summary()
 
     # FP64 product once, and the error of the mixed result against it

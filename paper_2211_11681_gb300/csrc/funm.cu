@@ -262,9 +262,11 @@ extern "C" s_status s_funm(s_pattern p, s_fn fn, const double* A, double* F, con
       std::vector<double> dk(steps);
       SF_CUDA(cudaMemcpyAsync(dk.data(), bN.p, sizeof(double) * steps, cudaMemcpyDeviceToHost, st));
       SF_CUDA(cudaStreamSynchronize(st));
-      for (int k = 2; k < steps; ++k)
-        if (dk[k] > 2.25 * dk[k - 1] && dk[k - 1] > 2.25 * dk[k - 2])   // squared norms: 1.5^2
+      for (int k = 0; k < steps; ++k) {
+        const bool grew = k >= 2 && dk[k] > 2.25 * dk[k - 1] && dk[k - 1] > 2.25 * dk[k - 2];  // squared norms: 1.5^2
+        if (!std::isfinite(dk[k]) || grew)
           return set_error(S_ERR_NOT_CONVERGED, "s_funm: Newton-Schulz iteration diverged at step " + std::to_string(k));
+      }
     }
     if (o.residual) {
       // ||P_S(F F) - A||_F / ||A||_F in double

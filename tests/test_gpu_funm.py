@@ -93,3 +93,19 @@ def test_mixed_exp_double_squarings(sphere):
     sf.funm(P, "exp_neg", dev(A.val), F, prec="fp32")
     E = ofunm.expm_taylor(A, sign=-1.0, nthreads=8)
     assert rel_frob(host(F), E.val) <= 1e-5
+
+
+def test_divergence_is_reported(sphere):
+    # a scaling c far below lambda_max puts eigenvalues of A/c beyond the Newton-Schulz
+    # region of convergence: the driver returns S_ERR_NOT_CONVERGED (a host-side status)
+    from paper_2211_11681_gb300 import sformat as sf
+    c, levels = sphere
+    A = c.A
+    P = pattern_of(A, levels)
+    lam = ofunm.norm_estimate(A)
+    F = dev(np.zeros(len(A.val)))
+    with pytest.raises(sf.SFormatError) as e:
+        sf.funm(P, "sqrt", dev(A.val), F, steps=25, scale=0.2 * lam)
+    assert e.value.status == sf.S_ERR_NOT_CONVERGED
+    # the library stays usable afterwards
+    sf.funm(P, "sqrt", dev(A.val), F, steps=25)
