@@ -105,23 +105,26 @@ s_status s_plan_create(s_pattern A, s_pattern B, s_pattern C, s_prec prec, s_pla
 s_status s_plan_destroy(s_plan plan);
 /* Exact triple count and useful flop count of the plan's product. */
 s_status s_plan_stats(s_plan plan, int64_t* triples, double* flops);
-/* Autotuner of S_FP32 plans: times every float kernel variant (output tile edge, the
- * micro-tile of one lane, the lambda extent of a stage) on the given operands, three launches each after one warm-up,
- * and keeps the fastest for this plan's forward product.  C is overwritten.  *chosen
- * (optional) receives the variant index.  S_FP64 plans have one shape (no-op).
+/* Autotuner of S_FP32 and S_FP64_DF plans: times every kernel variant of the plan's
+ * arithmetic (output tile edge, the micro-tile of one lane, for float also the lambda extent
+ * of a stage) on the given operands, three launches each after one warm-up, and keeps the
+ * fastest for this plan's forward product.  C is overwritten.  *chosen (optional) receives
+ * the variant index.  S_FP64 and S_BF16X3 plans have one shape (no-op).
  * Synchronises the stream. */
 s_status s_plan_autotune(s_plan plan, const void* A, const void* B, void* C, void* stream, int* chosen);
-/* Selects float variant `variant` (0 .. s_plan_num_variants()-1) for the plan's forward
- * product by hand (S_FP32 plans only). */
+/* Selects kernel variant `variant` (0 .. s_plan_num_variants_of(plan)-1) for the plan's
+ * forward product by hand (S_FP32 and S_FP64_DF plans). */
 s_status s_plan_set_variant(s_plan plan, int variant);
+/* Number of float variants; number of variants of a plan's arithmetic (1 when fixed). */
 int s_plan_num_variants(void);
+int s_plan_num_variants_of(s_plan plan);
 /* Declares that A's values are symmetric (A(nu, lambda) = A(lambda, nu)^T, as for a kernel
  * matrix in samplet coordinates).  The forward product then reads A(nu, lambda) through the
  * stored block (lambda, nu), which the float kernel stages with contiguous 16-byte copies.
  * Checks that A's pattern is symmetric (S_ERR_PATTERN otherwise); the values are the
  * caller's promise.  symmetric = 0 restores the default. */
 s_status s_plan_set_symmetric_a(s_plan plan, int symmetric);
-/* Shape of a float variant (variant < 0: the plan's current one): output tile edge, the
+/* Shape of a variant of the plan's arithmetic (variant < 0: the current one): output tile edge, the
  * micro-tile of one lane, and the largest lambda extent staged at once (consecutive small
  * lambda blocks are packed into one stage up to this extent).  Any output may be NULL. */
 s_status s_plan_variant(s_plan plan, int variant, int* tile, int* micro_rows, int* micro_cols, int* stage_k);

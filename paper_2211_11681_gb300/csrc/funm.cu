@@ -195,6 +195,9 @@ extern "C" s_status s_funm(s_pattern p, s_fn fn, const double* A, double* F, con
       Ain = bA.p;
       if (prec == S_FP32 && (s = s_plan_autotune(plan, Ain, Ain, P, st, nullptr))) return s;  // kernel shape
     }
+    if (prec == S_FP64_DF) {
+      if ((s = s_plan_autotune(plan, A, A, P, st, nullptr))) return s;  // kernel shape
+    }
     // Y_0 = A / c, Z_0 = I
     if ((s = run_add(p, aprec, 1.0 / c, Ain, 0.0, nullptr, 0.0, Y, st))) return s;
     SF_CUDA(cudaMemsetAsync(Z, 0, w * nnz, st));

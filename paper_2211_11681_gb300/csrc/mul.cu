@@ -508,12 +508,11 @@ __device__ __forceinline__ void cp_async8(float2* dst, const float2* src) {
   asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(d), "l"(src));
 }
 
-template <bool TX, bool TY>
+template <int TT, bool TX, bool TY>
 __device__ __forceinline__ void stage_copy_df(const Stage& sg, const float2* __restrict__ X,
                                               const float2* __restrict__ Y, const int64_t* xvoff,
                                               const int64_t* yvoff, int ni, int nj, int r0, int c0, int th, int tw,
                                               int lane, float2* xs, float2* ys) {
-  constexpr int TT = kTile;
   const int nl = sg.nl, t0 = sg.t0;
   const int tk = min(TT, nl - t0);
   const float2* xb = X + xvoff[sg.bx];
@@ -532,13 +531,21 @@ __device__ __forceinline__ void stage_copy_df(const Stage& sg, const float2* __r
 }
 
 constexpr int kDfWarps = 4;
-constexpr size_t kDfSmem = sizeof(float2) * kDfWarps * 2 * 2 * kTile * kTile;  // [warp][buf][A|B][TT*TT]
+struct DfVariant {
+  int tt, mr, mc;
+};
+constexpr DfVariant kDfVariants[] = {{20, 4, 4}, {10, 2, 2}};
+constexpr int kNumDfVariants = 2;
+static size_t df_smem(int v) {  // [warp][buf][A|B][TT*TT] float2
+  return sizeof(float2) * kDfWarps * 2 * 2 * kDfVariants[v].tt * kDfVariants[v].tt;
+}
 
-template <bool TX, bool TY>
+template <int TT, int MR, int MC, bool TX, bool TY>
 __global__ void __launch_bounds__(kDfWarps * 32, 3) mul_df_kernel(MulArgs a, const float2* __restrict__ X,
                                                                   const float2* __restrict__ Y,
                                                                   double* __restrict__ C) {
-  constexpr int TT = kTile, MR = 4, MC = 4, GC = TT / MC, NA = (TT / MR) * GC;
+  constexpr int GC = TT / MC, NA = (TT / MR) * GC, NQ = MR * MC;
+  static_assert(TT % MR == 0 && TT % MC == 0 && NA <= 32, "bad micro-tile");
   extern __shared__ __align__(16) float2 dsm[];
   __shared__ Stage sStage[kDfWarps][kStages];
   const int lane = threadIdx.x & 31;
@@ -558,9 +565,9 @@ __global__ void __launch_bounds__(kDfWarps * 32, 3) mul_df_kernel(MulArgs a, con
     const int nu = a.c_brow[k], nup = a.c_col[k];
     const int ni = a.bsize[nu], nj = a.bsize[nup];
     const int th = min(TT, ni - tile.r0), tw = min(TT, nj - tile.c0);
-    float sh[16], sl[16], ph[16], pl[16];  // running total and lambda-block partial
+    float sh[NQ], sl[NQ], ph[NQ], pl[NQ];  // running total and lambda-block partial
 #pragma unroll
-    for (int q = 0; q < 16; ++q) sh[q] = sl[q] = ph[q] = pl[q] = 0.0f;
+    for (int q = 0; q < NQ; ++q) sh[q] = sl[q] = ph[q] = pl[q] = 0.0f;
     const int px1 = (int)a.x.ptr[nu + 1];
     int px = (int)a.x.ptr[nu];
     int py0 = (int)a.y.ptr[nup];
@@ -585,8 +592,8 @@ __global__ void __launch_bounds__(kDfWarps * 32, 3) mul_df_kernel(MulArgs a, con
       __syncwarp();
       if (nm == 0) continue;
       int m = 0, q = 0, buf = 0;
-      stage_copy_df<TX, TY>(st[0], X, Y, a.x.voff, a.y.voff, ni, nj, tile.r0, tile.c0, th, tw, lane, base,
-                            base + TT * TT);
+      stage_copy_df<TT, TX, TY>(st[0], X, Y, a.x.voff, a.y.voff, ni, nj, tile.r0, tile.c0, th, tw, lane, base,
+                                base + TT * TT);
       cp_commit();
       for (;;) {
         const Stage cur = st[m];
@@ -598,8 +605,8 @@ __global__ void __launch_bounds__(kDfWarps * 32, 3) mul_df_kernel(MulArgs a, con
           Stage sg = st[nm2];
           sg.t0 = (int16_t)(nq2 * TT);
           float2* nb = base + (buf ^ 1) * 2 * TT * TT;
-          stage_copy_df<TX, TY>(sg, X, Y, a.x.voff, a.y.voff, ni, nj, tile.r0, tile.c0, th, tw, lane, nb,
-                                nb + TT * TT);
+          stage_copy_df<TT, TX, TY>(sg, X, Y, a.x.voff, a.y.voff, ni, nj, tile.r0, tile.c0, th, tw, lane, nb,
+                                    nb + TT * TT);
           cp_commit();
           cp_wait<1>();
         } else {
@@ -611,17 +618,16 @@ __global__ void __launch_bounds__(kDfWarps * 32, 3) mul_df_kernel(MulArgs a, con
           const float2* xs = base + buf * 2 * TT * TT;
           const float2* ys = xs + TT * TT;
           for (int tt = 0; tt < tk; ++tt) {
-            float2 av[4], bv[4];
+            float2 av[MR], bv[MC];
 #pragma unroll
-            for (int u = 0; u < 4; ++u) {
-              av[u] = xs[tt * TT + rl + u];
-              bv[u] = ys[tt * TT + cl + u];
-            }
+            for (int u = 0; u < MR; ++u) av[u] = xs[tt * TT + rl + u];
 #pragma unroll
-            for (int ii = 0; ii < 4; ++ii)
+            for (int u = 0; u < MC; ++u) bv[u] = ys[tt * TT + cl + u];
 #pragma unroll
-              for (int jj = 0; jj < 4; ++jj) {
-                const int qq = ii * 4 + jj;
+            for (int ii = 0; ii < MR; ++ii)
+#pragma unroll
+              for (int jj = 0; jj < MC; ++jj) {
+                const int qq = ii * MC + jj;
                 const float p = av[ii].x * bv[jj].x;
                 float e = fmaf(av[ii].x, bv[jj].x, -p);
                 e = fmaf(av[ii].x, bv[jj].y, e);
@@ -637,7 +643,7 @@ __global__ void __launch_bounds__(kDfWarps * 32, 3) mul_df_kernel(MulArgs a, con
         if (last_slice) {
           // (sh, sl) += (ph, pl): two-sum of the high words, low words added, renormalised
 #pragma unroll
-          for (int qq = 0; qq < 16; ++qq) {
+          for (int qq = 0; qq < NQ; ++qq) {
             const float s1 = sh[qq] + ph[qq];
             const float bp = s1 - sh[qq];
             const float e1 = ((sh[qq] - (s1 - bp)) + (ph[qq] - bp)) + (sl[qq] + pl[qq]);
@@ -656,12 +662,12 @@ __global__ void __launch_bounds__(kDfWarps * 32, 3) mul_df_kernel(MulArgs a, con
     if (active) {
       double* cb = C + a.c_voff[k];
 #pragma unroll
-      for (int ii = 0; ii < 4; ++ii)
+      for (int ii = 0; ii < MR; ++ii)
 #pragma unroll
-        for (int jj = 0; jj < 4; ++jj) {
+        for (int jj = 0; jj < MC; ++jj) {
           const int r = rl + ii, c = cl + jj;
           if (r < th && c < tw)
-            cb[(int64_t)(tile.r0 + r) * nj + tile.c0 + c] = (double)sh[ii * 4 + jj] + (double)sl[ii * 4 + jj];
+            cb[(int64_t)(tile.r0 + r) * nj + tile.c0 + c] = (double)sh[ii * MC + jj] + (double)sl[ii * MC + jj];
         }
     }
   }
@@ -1166,7 +1172,6 @@ static s_status launch_typed(const MulDesc& d, const void* X, const void* Y, voi
 
 static s_status launch_df(const MulDesc& d, const void* X, const void* Y, void* C, cudaStream_t st) {
   if (d.ntiles == 0) return S_OK;
-  if (d.edge != kTile) return set_error(S_ERR_ARG, "internal: double-float kernel needs 20-wide tiles");
   if (!d.df_x || !d.df_y) return set_error(S_ERR_ARG, "internal: double-float scratch missing");
   const int64_t nx = d.px->d.nnz, ny = d.py->d.nnz;
   const int gx = (int)std::max<int64_t>(1, std::min<int64_t>((nx + 255) / 256, (int64_t)num_sms() * 16));
@@ -1189,15 +1194,23 @@ static s_status launch_df(const MulDesc& d, const void* X, const void* Y, void* 
   a.counter = d.counter;
   SF_CUDA(cudaMemsetAsync(d.counter, 0, sizeof(unsigned int), st));
   using K = void (*)(MulArgs, const float2*, const float2*, double*);
-  K kern = d.x.trans ? (d.y.trans ? mul_df_kernel<true, true> : mul_df_kernel<true, false>)
-                     : (d.y.trans ? mul_df_kernel<false, true> : mul_df_kernel<false, false>);
-  SF_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kDfSmem));
+  const int v = d.variant < kNumDfVariants ? d.variant : 0;
+  if (d.edge != kDfVariants[v].tt) return set_error(S_ERR_ARG, "internal: tile list does not match variant");
+  K kern;
+  if (v == 1)
+    kern = d.x.trans ? (d.y.trans ? mul_df_kernel<10, 2, 2, true, true> : mul_df_kernel<10, 2, 2, true, false>)
+                     : (d.y.trans ? mul_df_kernel<10, 2, 2, false, true> : mul_df_kernel<10, 2, 2, false, false>);
+  else
+    kern = d.x.trans ? (d.y.trans ? mul_df_kernel<20, 4, 4, true, true> : mul_df_kernel<20, 4, 4, true, false>)
+                     : (d.y.trans ? mul_df_kernel<20, 4, 4, false, true> : mul_df_kernel<20, 4, 4, false, false>);
+  const size_t smem = df_smem(v);
+  SF_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   int per_sm = 0;
-  SF_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kDfWarps * 32, kDfSmem));
+  SF_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kDfWarps * 32, smem));
   if (per_sm < 1) per_sm = 1;
   const int64_t want = (d.ntiles + kDfWarps - 1) / kDfWarps;
   const int grid = (int)std::min<int64_t>(want, (int64_t)num_sms() * per_sm);
-  kern<<<grid, kDfWarps * 32, kDfSmem, st>>>(a, d.df_x, ysplit, (double*)C);
+  kern<<<grid, kDfWarps * 32, smem, st>>>(a, d.df_x, ysplit, (double*)C);
   SF_CUDA(cudaGetLastError());
   return S_OK;
 }
@@ -1340,10 +1353,13 @@ extern "C" s_status s_mul_masked_adjoint(s_plan p, const void* dC, const void* A
 
 extern "C" s_status s_plan_autotune(s_plan p, const void* A, const void* B, void* C, void* stream, int* chosen) {
   if (!p || !A || !B || !C) return set_error(S_ERR_ARG, "s_plan_autotune: NULL argument");
-  if (p->prec != S_FP32) {
+  if (p->prec != S_FP32 && p->prec != S_FP64_DF) {
     if (chosen) *chosen = 0;
-    return S_OK;  // one kernel shape for the double path
+    return S_OK;  // one kernel shape for the double and split-bfloat16 paths
   }
+  const bool df = p->prec == S_FP64_DF;
+  const int nvar = df ? kNumDfVariants : kNumF32Variants;
+  auto edge_of = [&](int v) { return df ? kDfVariants[v].tt : kF32Variants[v].tt; };
   cudaStream_t st = (cudaStream_t)stream;
   cudaEvent_t e0, e1;
   SF_CUDA(cudaEventCreate(&e0));
@@ -1351,12 +1367,12 @@ extern "C" s_status s_plan_autotune(s_plan p, const void* A, const void* B, void
   float best = 1e30f;
   int bestv = 0;
   s_status s = S_OK;
-  for (int v = 0; v < kNumF32Variants && !s; ++v) {
-    if ((s = build_tiles(&p->fwd, kF32Variants[v].tt))) break;
+  for (int v = 0; v < nvar && !s; ++v) {
+    if ((s = build_tiles(&p->fwd, edge_of(v)))) break;
     p->fwd.variant = v;
-    if ((s = run_mul(p->fwd, S_FP32, A, B, C, st))) break;  // warm-up
+    if ((s = run_mul(p->fwd, p->prec, A, B, C, st))) break;  // warm-up
     cudaEventRecord(e0, st);
-    for (int r = 0; r < 3 && !s; ++r) s = run_mul(p->fwd, S_FP32, A, B, C, st);
+    for (int r = 0; r < 3 && !s; ++r) s = run_mul(p->fwd, p->prec, A, B, C, st);
     cudaEventRecord(e1, st);
     cudaError_t e = cudaEventSynchronize(e1);
     if (e != cudaSuccess) {
@@ -1374,7 +1390,7 @@ extern "C" s_status s_plan_autotune(s_plan p, const void* A, const void* B, void
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   if (s) return s;
-  if ((s = build_tiles(&p->fwd, kF32Variants[bestv].tt))) return s;
+  if ((s = build_tiles(&p->fwd, edge_of(bestv)))) return s;
   p->fwd.variant = bestv;
   if (chosen) *chosen = bestv;
   return S_OK;
@@ -1384,6 +1400,14 @@ extern "C" s_status s_plan_variant(s_plan p, int variant, int* tile, int* micro_
                                    int* stage_k) {
   if (!p) return set_error(S_ERR_ARG, "s_plan_variant: NULL plan");
   if (variant < 0) variant = p->fwd.variant;
+  if (p->prec == S_FP64_DF) {
+    if (variant >= kNumDfVariants) return set_error(S_ERR_ARG, "s_plan_variant: no such variant");
+    if (tile) *tile = kDfVariants[variant].tt;
+    if (micro_rows) *micro_rows = kDfVariants[variant].mr;
+    if (micro_cols) *micro_cols = kDfVariants[variant].mc;
+    if (stage_k) *stage_k = kDfVariants[variant].tt;
+    return S_OK;
+  }
   if (variant >= kNumF32Variants) return set_error(S_ERR_ARG, "s_plan_variant: no such variant");
   if (tile) *tile = kF32Variants[variant].tt;
   if (micro_rows) *micro_rows = kF32Variants[variant].mr;
@@ -1394,15 +1418,22 @@ extern "C" s_status s_plan_variant(s_plan p, int variant, int* tile, int* micro_
 
 extern "C" s_status s_plan_set_variant(s_plan p, int variant) {
   if (!p) return set_error(S_ERR_ARG, "s_plan_set_variant: NULL plan");
-  if (variant < 0 || variant >= kNumF32Variants) return set_error(S_ERR_ARG, "s_plan_set_variant: no such variant");
-  if (p->prec != S_FP32) return set_error(S_ERR_ARG, "s_plan_set_variant: only float plans have variants");
-  s_status s = build_tiles(&p->fwd, kF32Variants[variant].tt);
+  if (p->prec != S_FP32 && p->prec != S_FP64_DF)
+    return set_error(S_ERR_ARG, "s_plan_set_variant: only float and double-float plans have variants");
+  const bool df = p->prec == S_FP64_DF;
+  if (variant < 0 || variant >= (df ? kNumDfVariants : kNumF32Variants))
+    return set_error(S_ERR_ARG, "s_plan_set_variant: no such variant");
+  s_status s = build_tiles(&p->fwd, df ? kDfVariants[variant].tt : kF32Variants[variant].tt);
   if (s) return s;
   p->fwd.variant = variant;
   return S_OK;
 }
 
 extern "C" int s_plan_num_variants(void) { return kNumF32Variants; }
+extern "C" int s_plan_num_variants_of(s_plan p) {
+  if (!p) return 0;
+  return p->prec == S_FP32 ? kNumF32Variants : (p->prec == S_FP64_DF ? kNumDfVariants : 1);
+}
 
 extern "C" s_status s_plan_set_symmetric_a(s_plan p, int symmetric) {
   if (!p) return set_error(S_ERR_ARG, "s_plan_set_symmetric_a: NULL plan");

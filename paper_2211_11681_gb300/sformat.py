@@ -48,6 +48,7 @@ def _load():
         "s_plan_set_variant": (i32, [vp, i32]),
         "s_plan_set_symmetric_a": (i32, [vp, i32]),
         "s_plan_num_variants": (i32, []),
+        "s_plan_num_variants_of": (i32, [vp]),
         "s_pattern_concat": (i32, [i32, P(vp), P(vp)]),
         "s_graph_capture_mul": (i32, [vp, vp, vp, vp, P(vp)]),
         "s_graph_launch": (i32, [vp, vp]),
@@ -187,6 +188,9 @@ class Plan:
     def set_symmetric_a(self, flag=True):
         """Caller asserts A is symmetric; the product reads A through its transposed index."""
         check(lib.s_plan_set_symmetric_a(self.h, 1 if flag else 0))
+
+    def num_variants(self):
+        return int(lib.s_plan_num_variants_of(self.h))
 
     def set_variant(self, v):
         check(lib.s_plan_set_variant(self.h, int(v)))

@@ -88,11 +88,13 @@ def test_general_patterns_and_ragged_tiles(sf, seed):
     o32 = dev(np.zeros(len(Cp.val)), "float32")
     p32.mul(dev(A.val, "float32"), dev(B.val, "float32"), o32)
     assert rel_frob(host(o32), want) <= 1e-5
-    # double-float arithmetic, forward and adjoint
+    # double-float arithmetic, every kernel shape, forward and adjoint
     pdf = sf.Plan(pa, pb, pc, "fp64_df")
-    odf = dev(np.full(len(Cp.val), np.nan))
-    pdf.mul(dev(A.val), dev(B.val), odf)
-    assert rel_frob(host(odf), want) <= 1e-12
+    for v in range(pdf.num_variants()):
+        pdf.set_variant(v)
+        odf = dev(np.full(len(Cp.val), np.nan))
+        pdf.mul(dev(A.val), dev(B.val), odf)
+        assert rel_frob(host(odf), want) <= 1e-12, v
     # adjoint
     dC = Cp.like(W.random_values(len(Cp.val), seed + 99))
     gA, gB = dev(np.zeros(len(A.val))), dev(np.zeros(len(B.val)))
