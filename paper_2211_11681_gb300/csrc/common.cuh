@@ -80,6 +80,10 @@ struct MulDesc {
   int64_t ntiles = 0;
   int edge = 20;             // tile edge of the list
   int variant = 0;           // float kernel variant (autotuned)
+  Tile* ptiles = nullptr;    // row-panel variants: tiles ordered by (row, r0, column)
+  int2* pidx = nullptr;      // per panel: first tile in ptiles, tile count
+  int64_t npanels = 0;
+  int panel_edge = 0, panel_size = 0;
   float2* df_x = nullptr;    // S_FP64_DF: split operands (hi, lo)
   float2* df_y = nullptr;
   struct __nv_bfloat16* bf_x = nullptr;  // S_BF16X3: three bfloat16 planes per operand
@@ -112,5 +116,5 @@ struct s_plan_t {
   sf::MulDesc adjA;  // dA = P_{S_A}(dC B^T), built on first use
   sf::MulDesc adjB;  // dB = P_{S_B}(A^T dC)
   bool adj_built = false;
-  float tune_ms[8] = {0};
+  float tune_ms[16] = {0};
 };

@@ -961,13 +961,294 @@ __global__ void __launch_bounds__(kTcWarps * 32, 2) mul_bf16x3_kernel(MulArgs a,
   }
 }
 
+// Row-panel float product for small blocks.  One warp owns up to P consecutive output
+// tiles of one block row: the same rows r0 .. r0 + th of block row nu, in different column
+// blocks nu'_j.  For every lambda of row nu the slice of op(X)(nu, lambda) is staged once
+// and reused by each member j whose block (lambda, nu'_j) exists in op(Y); absent members
+// skip both the copy and the FMAs.  Lane (mr, mc) owns the same MR x MC micro-position in
+// every member tile.  The lambda listing (ballot plus one binary search per member),
+// cp.async double buffering and the compensated lambda sums follow the tile kernel.
+constexpr int kPMax = 4;
+struct PStage {
+  int32_t bx;
+  int16_t nl, pad;
+  int32_t by[kPMax];  // -1: block (lambda, nu'_j) absent
+};
+
+struct PanelArgs {
+  const Tile* ptiles;
+  const int2* pidx;  // (first tile, tile count) of each panel
+  int64_t npanels;
+};
+
+// Slice [t0, t0 + wd) of op(X)(nu, lambda), rows r0 .. r0 + th, into xs[k][r] (k-major).
+template <int TT, bool TX>
+__device__ __forceinline__ void panel_copy_x(const float* xb, int t0, int wd, int ni, int nl, int r0, int th,
+                                             int lane, float* xs) {
+  const bool xvec = TT % 4 == 0 && TX && r0 == 0 && th == ni && (ni & 3) == 0 &&
+                    ((reinterpret_cast<uintptr_t>(xb) & 15) == 0);
+  if (xvec) {
+    const float rni = 1.0f / (float)ni;
+    for (int q = lane; q < (wd * ni) >> 2; q += 32) {
+      const int e = q << 2;
+      const int tt = __float2int_rz(((float)e + 0.5f) * rni), r = e - tt * ni;
+      cp_async16(xs + tt * TT + r, xb + (int64_t)(t0 + tt) * ni + r);
+    }
+  } else {
+    const float rwd = 1.0f / (float)wd;
+    for (int e = lane; e < th * wd; e += 32) {
+      const int r = __float2int_rz(((float)e + 0.5f) * rwd), tt = e - r * wd;
+      const int gr = r0 + r, gt = t0 + tt;
+      cp_async4(xs + tt * TT + r, TX ? xb + (int64_t)gt * ni + gr : xb + (int64_t)gr * nl + gt);
+    }
+  }
+}
+
+// Slice [t0, t0 + wd) of op(Y)(lambda, nu'), columns c0 .. c0 + tw, into ys[k][c].
+template <int TT, bool TY>
+__device__ __forceinline__ void panel_copy_y(const float* yb, int t0, int wd, int nj, int nl, int c0, int tw,
+                                             int lane, float* ys) {
+  const bool vec = TT % 4 == 0 && !TY && c0 == 0 && tw == nj && (nj & 3) == 0 &&
+                   ((reinterpret_cast<uintptr_t>(yb) & 15) == 0);
+  if (vec) {
+    const float rnj = 1.0f / (float)nj;
+    for (int q = lane; q < (wd * nj) >> 2; q += 32) {
+      const int e = q << 2;
+      const int tt = __float2int_rz(((float)e + 0.5f) * rnj), c = e - tt * nj;
+      cp_async16(ys + tt * TT + c, yb + (int64_t)(t0 + tt) * nj + c);
+    }
+  } else {
+    const float rtw = 1.0f / (float)tw;
+    for (int e = lane; e < wd * tw; e += 32) {
+      const int tt = __float2int_rz(((float)e + 0.5f) * rtw), c = e - tt * tw;
+      const int gt = t0 + tt, gc = c0 + c;
+      cp_async4(ys + tt * TT + c, TY ? yb + (int64_t)gc * nl + gt : yb + (int64_t)gt * nj + gc);
+    }
+  }
+}
+
+template <int TT, int MR, int MC, int P, bool TX, bool TY>
+__global__ void __launch_bounds__(kF32Warps * 32, 4) mul_f32_panel_kernel(MulArgs a, PanelArgs pa,
+                                                                          const float* __restrict__ X,
+                                                                          const float* __restrict__ Y,
+                                                                          float* __restrict__ C) {
+  constexpr int GR = TT / MR, GC = TT / MC, NA = GR * GC, NQ = MR * MC, BUF = (1 + P) * TT * TT;
+  static_assert(TT % MR == 0 && TT % MC == 0 && NA <= 32 && TT % 2 == 0 && P >= 1 && P <= kPMax &&
+                    (MR != 4 || TT % 4 == 0) && (MC != 4 || TT % 4 == 0),
+                "bad panel shape");
+  extern __shared__ __align__(16) float psm[];  // [warp][buf][X | Y_0 .. Y_{P-1}][TT * TT]
+  __shared__ PStage sSt[kF32Warps][kStages];
+  const int lane = threadIdx.x & 31;
+  const int w = threadIdx.x >> 5;
+  float* wbase = psm + (size_t)w * 2 * BUF;
+  PStage* st = sSt[w];
+  const bool active = lane < NA;
+  const int mr = active ? lane / GC : 0, mc = active ? lane % GC : 0;
+  const int rl = MR * mr, cl = MC * mc;
+  for (;;) {
+    unsigned int t = 0;
+    if (lane == 0) t = atomicAdd(a.counter, 1u);
+    t = __shfl_sync(0xffffffffu, t, 0);
+    if (t >= pa.npanels) break;
+    const int2 pi = pa.pidx[t];
+    const Tile* tl = pa.ptiles + pi.x;
+    const int cnt = pi.y;
+    const int nu = a.c_brow[tl[0].blk];
+    const int ni = a.bsize[nu];
+    const int r0 = tl[0].r0;
+    const int th = min(TT, ni - r0);
+    int kj[P], njv[P], c0v[P], twv[P], py0[P], py1[P];
+#pragma unroll
+    for (int j = 0; j < P; ++j) {
+      kj[j] = -1, njv[j] = 0, c0v[j] = 0, twv[j] = 0, py0[j] = 0, py1[j] = 0;
+      if (j < cnt) {
+        const Tile tj = tl[j];
+        const int nup = a.c_col[tj.blk];
+        kj[j] = tj.blk;
+        njv[j] = a.bsize[nup];
+        c0v[j] = tj.c0;
+        twv[j] = min(TT, njv[j] - c0v[j]);
+        py0[j] = (int)a.y.ptr[nup];
+        py1[j] = (int)a.y.ptr[nup + 1];
+      }
+    }
+    float acc[P][NQ], comp[P][NQ], p[P][NQ];
+#pragma unroll
+    for (int j = 0; j < P; ++j)
+#pragma unroll
+      for (int q = 0; q < NQ; ++q) acc[j][q] = comp[j][q] = p[j][q] = 0.0f;
+    int folded = 0;  // lambda blocks summed into p since the last two-sum
+    const int px1 = (int)a.x.ptr[nu + 1];
+    int px = (int)a.x.ptr[nu];
+    while (px < px1) {
+      // ---- list up to kStages lambdas that meet at least one member ---------------------
+      int nm = 0;
+      while (px < px1 && nm <= kStages - 32) {
+        const int i = px + lane;
+        const int32_t lam = i < px1 ? __ldg(a.x.idx + i) : INT32_MAX;
+        PStage ps;
+        bool any = false;
+#pragma unroll
+        for (int j = 0; j < kPMax; ++j) ps.by[j] = -1;
+#pragma unroll
+        for (int j = 0; j < P; ++j) {
+          if (j < cnt) {
+            const int pos = lower_bound_dev(a.y.idx, py0[j], py1[j], lam);
+            const bool hit = i < px1 && pos < py1[j] && __ldg(a.y.idx + pos) == lam;
+            if (hit) ps.by[j] = a.y.blk ? __ldg(a.y.blk + pos) : pos;
+            any |= hit;
+            py0[j] = __shfl_sync(0xffffffffu, pos, 31);
+          }
+        }
+        const unsigned int mask = __ballot_sync(0xffffffffu, any);
+        if (any) {
+          ps.bx = a.x.blk ? __ldg(a.x.blk + i) : i;
+          ps.nl = (int16_t)a.bsize[lam];
+          ps.pad = 0;
+          st[nm + __popc(mask & ((1u << lane) - 1u))] = ps;
+        }
+        nm += __popc(mask);
+        px += 32;
+      }
+      __syncwarp();
+      if (nm == 0) continue;
+      // ---- stream TT-wide slices of the listed lambdas; the next slice's copies overlap
+      // ---- the current slice's FMAs
+      auto issue = [&](int m, int t0, float* b) {
+        const PStage& sg = st[m];
+        const int wd = min(TT, (int)sg.nl - t0);
+        panel_copy_x<TT, TX>(X + a.x.voff[sg.bx], t0, wd, ni, sg.nl, r0, th, lane, b);
+#pragma unroll
+        for (int j = 0; j < P; ++j)
+          if (sg.by[j] >= 0)
+            panel_copy_y<TT, TY>(Y + a.y.voff[sg.by[j]], t0, wd, njv[j], sg.nl, c0v[j], twv[j], lane,
+                                 b + (1 + j) * TT * TT);
+        cp_commit();
+      };
+      int m = 0, t0 = 0, buf = 0;
+      issue(0, 0, wbase);
+      for (;;) {
+        const PStage cur = st[m];
+        const bool last_slice = t0 + TT >= (int)cur.nl;
+        const int m2 = last_slice ? m + 1 : m, t2 = last_slice ? 0 : t0 + TT;
+        const bool more = m2 < nm;
+        if (more) {
+          issue(m2, t2, wbase + (buf ^ 1) * BUF);
+          cp_wait<1>();
+        } else {
+          cp_wait<0>();
+        }
+        __syncwarp();
+        const int tk = min(TT, (int)cur.nl - t0);
+        if (active) {
+          const float* xs = wbase + buf * BUF;
+          for (int tt = 0; tt < tk; ++tt) {
+            float ar[MR];
+            lds<MR>(xs + tt * TT + rl, ar);
+#pragma unroll
+            for (int j = 0; j < P; ++j) {
+              if (cur.by[j] >= 0) {
+                float br[MC];
+                lds<MC>(xs + (1 + j) * TT * TT + tt * TT + cl, br);
+#pragma unroll
+                for (int ii = 0; ii < MR; ++ii)
+#pragma unroll
+                  for (int jj = 0; jj < MC; ++jj) p[j][ii * MC + jj] = fmaf(ar[ii], br[jj], p[j][ii * MC + jj]);
+              }
+            }
+          }
+        }
+        __syncwarp();
+        if (last_slice && ++folded == kFold) {
+          folded = 0;
+#pragma unroll
+          for (int j = 0; j < P; ++j)
+#pragma unroll
+            for (int q = 0; q < NQ; ++q) {
+              const float hi = acc[j][q] + p[j][q];
+              const float bp = hi - acc[j][q];
+              comp[j][q] += (acc[j][q] - (hi - bp)) + (p[j][q] - bp);
+              acc[j][q] = hi;
+              p[j][q] = 0.0f;
+            }
+        }
+        if (!more) break;
+        m = m2;
+        t0 = t2;
+        buf ^= 1;
+      }
+    }
+    if (active) {
+#pragma unroll
+      for (int j = 0; j < P; ++j) {
+        if (j < cnt) {
+          float* cb = C + a.c_voff[kj[j]];
+#pragma unroll
+          for (int ii = 0; ii < MR; ++ii)
+#pragma unroll
+            for (int jj = 0; jj < MC; ++jj) {
+              const int q = ii * MC + jj;
+              const float hi = acc[j][q] + p[j][q];
+              const float bp = hi - acc[j][q];
+              const float err = (acc[j][q] - (hi - bp)) + (p[j][q] - bp);
+              const int r = rl + ii, c = cl + jj;
+              if (r < th && c < twv[j]) cb[(int64_t)(r0 + r) * njv[j] + c0v[j] + c] = hi + (comp[j][q] + err);
+            }
+        }
+      }
+    }
+  }
+}
+
+// Panel list of S_C for tile edge `edge` and at most `P` tiles per panel: for every block
+// row nu and row offset r0, the column tiles of the row's blocks in column order, cut into
+// runs of P.
+static s_status build_panels(MulDesc* d, int edge, int P) {
+  const s_pattern_t* C = d->pc;
+  cudaFree(d->ptiles);
+  cudaFree(d->pidx);
+  d->ptiles = nullptr;
+  d->pidx = nullptr;
+  d->npanels = 0;
+  std::vector<Tile> tl;
+  std::vector<int2> idx;
+  for (int32_t nu = 0; nu < C->d.nc; ++nu) {
+    const int ni = C->bsize[nu];
+    for (int r0 = 0; r0 < ni; r0 += edge) {
+      int run = 0;
+      for (int64_t k = C->rowptr[nu]; k < C->rowptr[nu + 1]; ++k) {
+        const int nj = C->bsize[C->colidx[k]];
+        for (int c0 = 0; c0 < nj; c0 += edge) {
+          if (run == 0) idx.push_back(make_int2((int)tl.size(), 0));
+          tl.push_back(Tile{(int32_t)k, (int16_t)r0, (int16_t)c0});
+          idx.back().y++;
+          if (++run == P) run = 0;
+        }
+      }
+    }
+  }
+  cudaError_t e = cudaMalloc(&d->ptiles, sizeof(Tile) * std::max<size_t>(tl.size(), 1));
+  if (e == cudaSuccess) e = cudaMalloc(&d->pidx, sizeof(int2) * std::max<size_t>(idx.size(), 1));
+  if (e == cudaSuccess && !tl.empty())
+    e = cudaMemcpy(d->ptiles, tl.data(), sizeof(Tile) * tl.size(), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess && !idx.empty())
+    e = cudaMemcpy(d->pidx, idx.data(), sizeof(int2) * idx.size(), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) return cuda_error(e, "build_panels");
+  d->npanels = (int64_t)idx.size();
+  d->panel_edge = edge;
+  d->panel_size = P;
+  return S_OK;
+}
+
 // The float kernel variants the autotuner chooses from: tile edge and lane micro-tile.
 struct F32Variant {
   int tt, mr, mc, km;  // tile edge, lane micro-tile, largest lambda extent of one stage
+  int panel;           // 0: one tile per warp; P > 0: row panels of up to P tiles per warp
 };
-constexpr F32Variant kF32Variants[] = {{20, 4, 4, 20}, {20, 4, 4, 40}, {16, 4, 2, 32}, {12, 3, 2, 36},
-                                       {10, 2, 2, 40}, {8, 2, 1, 32}};
-constexpr int kNumF32Variants = 6;
+constexpr F32Variant kF32Variants[] = {{20, 4, 4, 20, 0}, {20, 4, 4, 40, 0}, {16, 4, 2, 32, 0},
+                                       {12, 3, 2, 36, 0}, {10, 2, 2, 40, 0}, {8, 2, 1, 32, 0},
+                                       {12, 3, 2, 12, 3}, {10, 2, 2, 10, 4}, {8, 2, 1, 8, 4}};
+constexpr int kNumF32Variants = 9;
 
 static int g_sms = 0;
 static int num_sms() {
@@ -1095,6 +1376,11 @@ s_status build_desc(const s_pattern_t* X, bool tx, const s_pattern_t* Y, bool ty
 }
 
 void free_desc(MulDesc* d) {
+  cudaFree(d->ptiles);
+  cudaFree(d->pidx);
+  d->ptiles = nullptr;
+  d->pidx = nullptr;
+  d->npanels = 0;
   cudaFree(d->tiles);
   cudaFree(d->counter);
   cudaFree(d->df_x);
@@ -1117,6 +1403,16 @@ static F32Kernel f32_kernel(bool tx, bool ty) {
             : (ty ? mul_f32_kernel<TT, MR, MC, KM, false, true> : mul_f32_kernel<TT, MR, MC, KM, false, false>);
 }
 
+using F32PanelKernel = void (*)(MulArgs, PanelArgs, const float*, const float*, float*);
+template <int V>
+static F32PanelKernel f32_panel_kernel(bool tx, bool ty) {
+  constexpr int TT = kF32Variants[V].tt, MR = kF32Variants[V].mr, MC = kF32Variants[V].mc,
+                P = kF32Variants[V].panel;
+  return tx ? (ty ? mul_f32_panel_kernel<TT, MR, MC, P, true, true> : mul_f32_panel_kernel<TT, MR, MC, P, true, false>)
+            : (ty ? mul_f32_panel_kernel<TT, MR, MC, P, false, true>
+                  : mul_f32_panel_kernel<TT, MR, MC, P, false, false>);
+}
+
 static F32Kernel f32_kernel_of(int v, bool tx, bool ty) {
   switch (v) {
     case 1: return f32_kernel<1>(tx, ty);
@@ -1128,7 +1424,43 @@ static F32Kernel f32_kernel_of(int v, bool tx, bool ty) {
   }
 }
 
-static size_t f32_smem(int v) { return sizeof(float) * kF32Warps * 4 * kF32Variants[v].km * kF32Variants[v].tt; }
+static size_t f32_smem(int v) {
+  const F32Variant& f = kF32Variants[v];
+  if (f.panel) return sizeof(float) * kF32Warps * 2 * (1 + f.panel) * f.tt * f.tt;
+  return sizeof(float) * kF32Warps * 4 * f.km * f.tt;
+}
+
+static s_status launch_f32_panel(const MulDesc& d, const void* X, const void* Y, void* C, cudaStream_t st) {
+  const F32Variant& f = kF32Variants[d.variant];
+  if (d.panel_edge != f.tt || d.panel_size != f.panel || !d.pidx)
+    return set_error(S_ERR_ARG, "internal: panel list does not match variant");
+  if (d.npanels == 0) return S_OK;
+  MulArgs a;
+  a.x = dev_side(d.x);
+  a.y = dev_side(d.y);
+  a.bsize = d.pc->d.bsize;
+  a.c_brow = d.pc->d.brow;
+  a.c_col = d.pc->d.colidx;
+  a.c_voff = d.pc->d.voff;
+  a.tiles = d.tiles;
+  a.ntiles = d.ntiles;
+  a.counter = d.counter;
+  SF_CUDA(cudaMemsetAsync(d.counter, 0, sizeof(unsigned int), st));
+  F32PanelKernel kern = d.variant == 6   ? f32_panel_kernel<6>(d.x.trans, d.y.trans)
+                        : d.variant == 7 ? f32_panel_kernel<7>(d.x.trans, d.y.trans)
+                                         : f32_panel_kernel<8>(d.x.trans, d.y.trans);
+  const size_t smem = f32_smem(d.variant);
+  SF_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  int per_sm = 0;
+  SF_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kF32Warps * 32, smem));
+  if (per_sm < 1) per_sm = 1;
+  const int64_t want = (d.npanels + kF32Warps - 1) / kF32Warps;
+  const int grid = (int)std::min<int64_t>(want, (int64_t)num_sms() * per_sm);
+  kern<<<grid, kF32Warps * 32, smem, st>>>(a, PanelArgs{d.ptiles, d.pidx, d.npanels}, (const float*)X,
+                                           (const float*)Y, (float*)C);
+  SF_CUDA(cudaGetLastError());
+  return S_OK;
+}
 
 template <typename T>
 static s_status launch_typed(const MulDesc& d, const void* X, const void* Y, void* C, cudaStream_t st) {
@@ -1150,6 +1482,7 @@ static s_status launch_typed(const MulDesc& d, const void* X, const void* Y, voi
   int warps;
   size_t dsmem = 0;
   if constexpr (sizeof(T) == 4) {
+    if (kF32Variants[d.variant].panel) return launch_f32_panel(d, X, Y, C, st);
     if (d.edge != kF32Variants[d.variant].tt) return set_error(S_ERR_ARG, "internal: tile list does not match variant");
     kern = f32_kernel_of(d.variant, d.x.trans, d.y.trans);
     warps = kF32Warps;
@@ -1367,8 +1700,15 @@ extern "C" s_status s_plan_autotune(s_plan p, const void* A, const void* B, void
   float best = 1e30f;
   int bestv = 0;
   s_status s = S_OK;
+  // Row panels pay off only when most blocks of S_C are at most one tile wide: skip them
+  // when the root-mean-square block edge of S_C exceeds the panel's tile edge.
+  const s_pattern_t* pc = p->fwd.pc;
+  const double rms_edge = std::sqrt((double)pc->d.nnz / (double)std::max<int64_t>(pc->d.nblocks, 1));
   for (int v = 0; v < nvar && !s; ++v) {
+    const bool panel = !df && kF32Variants[v].panel;
+    if (panel && rms_edge > kF32Variants[v].tt) continue;
     if ((s = build_tiles(&p->fwd, edge_of(v)))) break;
+    if (panel && (s = build_panels(&p->fwd, kF32Variants[v].tt, kF32Variants[v].panel))) break;
     p->fwd.variant = v;
     if ((s = run_mul(p->fwd, p->prec, A, B, C, st))) break;  // warm-up
     cudaEventRecord(e0, st);
@@ -1391,6 +1731,9 @@ extern "C" s_status s_plan_autotune(s_plan p, const void* A, const void* B, void
   cudaEventDestroy(e1);
   if (s) return s;
   if ((s = build_tiles(&p->fwd, edge_of(bestv)))) return s;
+  if (!df && kF32Variants[bestv].panel &&
+      (s = build_panels(&p->fwd, kF32Variants[bestv].tt, kF32Variants[bestv].panel)))
+    return s;
   p->fwd.variant = bestv;
   if (chosen) *chosen = bestv;
   return S_OK;
@@ -1424,6 +1767,8 @@ extern "C" s_status s_plan_set_variant(s_plan p, int variant) {
   if (variant < 0 || variant >= (df ? kNumDfVariants : kNumF32Variants))
     return set_error(S_ERR_ARG, "s_plan_set_variant: no such variant");
   s_status s = build_tiles(&p->fwd, df ? kDfVariants[variant].tt : kF32Variants[variant].tt);
+  if (!s && !df && kF32Variants[variant].panel)
+    s = build_panels(&p->fwd, kF32Variants[variant].tt, kF32Variants[variant].panel);
   if (s) return s;
   p->fwd.variant = variant;
   return S_OK;
