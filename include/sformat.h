@@ -57,8 +57,12 @@ typedef enum {
  *              error-free transformations; about 2^-44 relative per operation.
  *   S_FP32     float in, float out, float multiply-add.
  *   S_BF16X3   float in, float out; each operand split into three bfloat16 parts,
- *              the six leading cross products on the tensor cores, float accumulate. */
-typedef enum { S_FP64 = 0, S_FP32 = 1, S_BF16X3 = 2, S_FP64_DF = 3 } s_prec;
+ *              the six leading cross products on the tensor cores, float accumulate.
+ *   S_TF32X3   float in, float out; each operand split as hi + lo, both rounded to TF32
+ *              (10 fraction bits), the three products hi*hi + hi*lo + lo*hi on the tcgen05
+ *              tensor cores, the sums over lambda accumulated in fp32 in tensor memory.
+ *              Blocks may be at most 96 wide.  Inputs must be finite. */
+typedef enum { S_FP64 = 0, S_FP32 = 1, S_BF16X3 = 2, S_FP64_DF = 3, S_TF32X3 = 4 } s_prec;
 
 typedef enum { S_SQRT = 0, S_EXP = 1, S_EXP_NEG = 2 } s_fn;
 
@@ -122,7 +126,10 @@ int s_plan_num_variants_of(s_plan plan);
  * matrix in samplet coordinates).  The forward product then reads A(nu, lambda) through the
  * stored block (lambda, nu), which the float kernel stages with contiguous 16-byte copies.
  * Checks that A's pattern is symmetric (S_ERR_PATTERN otherwise); the values are the
- * caller's promise.  symmetric = 0 restores the default. */
+ * caller's promise.  symmetric = 0 restores the default.  For an S_TF32X3 plan the flag
+ * needs B's pattern to be A's and the product to be called with B = A (the same buffer);
+ * the kernel then reads B(lambda, nu') through the stored block (nu', lambda) and both
+ * operands from one set of split planes. */
 s_status s_plan_set_symmetric_a(s_plan plan, int symmetric);
 /* Shape of a variant of the plan's arithmetic (variant < 0: the current one): output tile edge, the
  * micro-tile of one lane, and the largest lambda extent staged at once (consecutive small

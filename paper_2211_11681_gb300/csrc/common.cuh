@@ -71,6 +71,23 @@ struct Tile {
   int16_t c0;   // first column
 };
 
+// S_TF32X3 product (mul_tc.cu): MMA rows (member columns) and columns (own rows) of a panel,
+// members per panel, lambda extent of one stage, widest block supported.
+constexpr int kTcM = 128;
+constexpr int kTcN = 32;
+constexpr int kTcP = 8;
+constexpr int kTcKC = 24;
+constexpr int kTcMaxB = 96;
+
+// One stage of an S_TF32X3 panel: source offsets (in the split value planes) of the X slice
+// and of each member's Y slice (-1: member has no block for this lambda), lambda's block
+// size (row pitch of the slices) and the staged extent.
+struct TcEntry {
+  int64_t x;
+  int64_t y[kTcP];
+  int32_t nl, wd;
+};
+
 struct MulDesc {
   Side x, y;                 // C = op(X) op(Y) on S_C
   const s_pattern_t* pc;
@@ -84,6 +101,15 @@ struct MulDesc {
   int2* pidx = nullptr;      // per panel: first tile in ptiles, tile count
   int64_t npanels = 0;
   int panel_edge = 0, panel_size = 0;
+  int64_t* tc_pstart = nullptr;  // S_TF32X3: first stage of each panel (npanels + 1)
+  TcEntry* tc_ent = nullptr;     // S_TF32X3: stages of all panels
+  int64_t tc_nentries = 0;
+  float* tc_xh = nullptr;        // S_TF32X3 split planes (hi, lo) of both operands
+  float* tc_xl = nullptr;
+  float* tc_yh = nullptr;
+  float* tc_yl = nullptr;
+  unsigned int* tc_err = nullptr;  // set when a bounded wait of the kernel ran out
+  bool tc_sym = false;             // symmetric plan: B = A, Y read through its stored transpose
   float2* df_x = nullptr;    // S_FP64_DF: split operands (hi, lo)
   float2* df_y = nullptr;
   struct __nv_bfloat16* bf_x = nullptr;  // S_BF16X3: three bfloat16 planes per operand
@@ -96,6 +122,9 @@ struct MulDesc {
 s_status build_desc(const s_pattern_t* X, bool tx, const s_pattern_t* Y, bool ty, const s_pattern_t* C, s_prec prec,
                     MulDesc* d);
 void free_desc(MulDesc* d);
+s_status tc_prepare(MulDesc* d);
+void tc_free(MulDesc* d);
+s_status launch_tc(const MulDesc& d, const void* X, const void* Y, void* C, cudaStream_t st);
 s_status run_mul(const MulDesc& d, s_prec prec, const void* X, const void* Y, void* C, cudaStream_t st);
 
 // Element-wise kernels (add.cu)

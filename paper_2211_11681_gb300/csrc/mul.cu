@@ -1361,6 +1361,7 @@ s_status build_desc(const s_pattern_t* X, bool tx, const s_pattern_t* Y, bool ty
       if (e != cudaSuccess) st = cuda_error(e, "cudaMalloc(split-bfloat16 scratch)");
     }
   }
+  if (!st && prec == S_TF32X3) st = tc_prepare(&d);
   if (!st && prec == S_FP64_DF) {
     // split operands (float pairs), reused by every call of this plan
     e = cudaMalloc(&d.df_x, sizeof(float2) * std::max<int64_t>(X->d.nnz, 1));
@@ -1376,6 +1377,9 @@ s_status build_desc(const s_pattern_t* X, bool tx, const s_pattern_t* Y, bool ty
 }
 
 void free_desc(MulDesc* d) {
+  tc_free(d);
+  cudaFree(d->tc_err);
+  d->tc_err = nullptr;
   cudaFree(d->ptiles);
   cudaFree(d->pidx);
   d->ptiles = nullptr;
@@ -1597,6 +1601,8 @@ s_status run_mul(const MulDesc& d, s_prec prec, const void* X, const void* Y, vo
       return launch_df(d, X, Y, C, st);
     case S_BF16X3:
       return launch_bf16x3(d, X, Y, C, st);
+    case S_TF32X3:
+      return launch_tc(d, X, Y, C, st);
     default:
       return set_error(S_ERR_ARG, "precision not supported by this product path");
   }
@@ -1616,7 +1622,7 @@ extern "C" s_status s_plan_create(s_pattern A, s_pattern B, s_pattern C, s_prec 
   if (!out) return set_error(S_ERR_ARG, "s_plan_create: out is NULL");
   *out = nullptr;
   if (!A || !B || !C) return set_error(S_ERR_ARG, "s_plan_create: NULL pattern");
-  if (prec != S_FP64 && prec != S_FP32 && prec != S_FP64_DF && prec != S_BF16X3)
+  if (prec != S_FP64 && prec != S_FP32 && prec != S_FP64_DF && prec != S_BF16X3 && prec != S_TF32X3)
     return set_error(S_ERR_ARG, "s_plan_create: unsupported precision");
   s_status st;
   if ((st = check_same_tree(A, B)) || (st = check_same_tree(A, C))) return st;
@@ -1751,6 +1757,13 @@ extern "C" s_status s_plan_variant(s_plan p, int variant, int* tile, int* micro_
     if (stage_k) *stage_k = kDfVariants[variant].tt;
     return S_OK;
   }
+  if (p->prec == S_TF32X3) {
+    if (tile) *tile = kTcN;
+    if (micro_rows) *micro_rows = kTcM;
+    if (micro_cols) *micro_cols = kTcN;
+    if (stage_k) *stage_k = kTcKC;
+    return S_OK;
+  }
   if (variant >= kNumF32Variants) return set_error(S_ERR_ARG, "s_plan_variant: no such variant");
   if (tile) *tile = kF32Variants[variant].tt;
   if (micro_rows) *micro_rows = kF32Variants[variant].mr;
@@ -1798,6 +1811,15 @@ extern "C" s_status s_plan_set_symmetric_a(s_plan p, int symmetric) {
         if (!std::binary_search(b, e, i))
           return set_error(S_ERR_PATTERN, "s_plan_set_symmetric_a: the pattern of A is not symmetric");
       }
+  }
+  if (p->prec == S_TF32X3) {
+    // the tensor-core kernel wants op(B)(lambda, nu') column by column along lambda's index:
+    // with B = A symmetric that is the stored block (nu', lambda), read through B's rows
+    if (symmetric && p->b != p->a)
+      return set_error(S_ERR_ARG, "s_plan_set_symmetric_a: an S_TF32X3 plan needs B's pattern to be A's");
+    p->fwd.y = side_of(p->b, false, symmetric != 0);
+    p->fwd.tc_sym = symmetric != 0;
+    return tc_prepare(&p->fwd);
   }
   // read A(nu, lambda) as the transpose of the stored block (lambda, nu): same values when A
   // is symmetric, and column-contiguous staging for the float kernel

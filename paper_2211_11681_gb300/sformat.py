@@ -15,10 +15,10 @@ LIB_PATH = os.path.join(HERE, "_lib", "libsformat.so")
 
 S_OK, S_ERR_ARG, S_ERR_PATTERN, S_ERR_MISMATCH, S_ERR_NOMEM, S_ERR_CUDA, S_ERR_NOT_CONVERGED, S_ERR_TIMEOUT = \
     0, -1, -2, -3, -4, -5, -6, -7
-S_FP64, S_FP32, S_BF16X3, S_FP64_DF = 0, 1, 2, 3
+S_FP64, S_FP32, S_BF16X3, S_FP64_DF, S_TF32X3 = 0, 1, 2, 3, 4
 S_SQRT, S_EXP, S_EXP_NEG = 0, 1, 2
 
-PREC = {"fp64": S_FP64, "fp32": S_FP32, "bf16x3": S_BF16X3, "fp64_df": S_FP64_DF}
+PREC = {"fp64": S_FP64, "fp32": S_FP32, "bf16x3": S_BF16X3, "fp64_df": S_FP64_DF, "tf32x3": S_TF32X3}
 
 
 class SFormatError(RuntimeError):
