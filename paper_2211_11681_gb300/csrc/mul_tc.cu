@@ -6,14 +6,17 @@
 // blocks (nu, nu'_j) of that row.  For every lambda of row nu of op(X) that meets at least one
 // member, one stage computes
 //     D[m][n] += sum_t Y_j(lambda)[c][t] * X(nu, lambda)[r0 + n][t],   m = moff_j + c,
-// a single M=128 x N=16|32 x K=8.. tcgen05.mma chain with the accumulator D in tensor memory:
-// the 128 member columns are the MMA rows and the panel's rows of nu the MMA columns, so the
-// X(nu, lambda) slice is staged once for all members.  Members without block (lambda, nu'_j)
+// a short M=128 x N=16|32 x K=8.. tcgen05.mma chain into a tensor-memory accumulator of its
+// own: the 128 member columns are the MMA rows and the panel's rows of nu the MMA columns, so
+// the X(nu, lambda) slice is staged once for all members.  Members without block (lambda, nu'_j)
 // get zero rows.  Each operand is split as x ~ hi + lo with hi = x rounded to TF32 (10
 // fraction bits) and lo = x - hi rounded to TF32; both are stored as fp32 words whose low 13
 // bits are zero, which is exactly what the tensor core reads of them.  The three products
 // hi*hi + hi*lo + lo*hi are exact in the MMA; the dropped lo*lo and the rounding of lo are each
-// below 2^-22 |x y|, with random signs.  Sums accumulate in fp32 in tensor memory.
+// below 2^-22 |x y|, with random signs.  The tensor core's fp32 accumulation drops low bits
+// with a bias, so each stage starts a fresh accumulator (at most 9 MMAs deep) and the stage
+// sums are added over lambda in registers with round-to-nearest; independent accumulators also
+// let the MMAs of consecutive stages overlap.
 //
 // Staging: operands are K-major in the tensor core's no-swizzle canonical layout (8-row x
 // 16-byte core matrices; K-adjacent core matrices 128 bytes apart, 8-row groups kTcSBO bytes
@@ -21,7 +24,9 @@
 // index t.  A pre-pass writes the split planes, per-block transposed where an operand's
 // stored orientation runs the other way.  kTcS stage buffers rotate; copies run kTcD stages
 // ahead of the MMAs, and an mbarrier per buffer (signalled by tcgen05.commit) tells when the
-// tensor core has finished reading it.
+// tensor core has finished the stage: its shared-memory buffer is free and its accumulator
+// (kTcN tensor-memory columns per buffer) can be read.  The stage entries of a panel come
+// into shared memory kTcE at a time, so no stage waits on a global load of its own entry.
 //
 // The stage list of every panel (which lambda, which members, source offsets) is built once
 // per plan on the device (symbolic phase).
@@ -34,14 +39,18 @@ namespace sf {
 namespace {
 
 constexpr int kTcThreads = 256;
-constexpr int kTcS = 5;                                    // stage buffers
-constexpr int kTcD = kTcS - 1;                             // copy lookahead in stages
+constexpr int kTcS = 6;                                    // stage buffers
+constexpr int kTcD = 4;                                    // copy lookahead in stages (< kTcS)
+constexpr int kTcE = 64;                                   // stage entries loaded at once
 constexpr uint32_t kTcSBO = kTcKC * 32;                    // bytes between 8-row groups
 constexpr uint32_t kTcAPlane = kTcM / 8 * kTcSBO;          // one plane of the member operand
 constexpr uint32_t kTcBPlane = kTcN / 8 * kTcSBO;          // one plane of the X operand
 constexpr uint32_t kTcBuf = 2 * kTcAPlane + 2 * kTcBPlane;  // hi, lo of both
 constexpr size_t kTcSmem = (size_t)kTcS * kTcBuf;
-static_assert(kTcKC % 8 == 0 && kTcSmem <= 200 * 1024, "stage buffers");
+constexpr int kTcCols = 256;                               // tensor-memory columns (>= kTcS * kTcN)
+static_assert(kTcS * kTcN <= kTcCols, "tensor memory");
+static_assert(kTcKC % 8 == 0 && kTcSmem <= 200 * 1024 && kTcD < kTcS, "stage buffers");
+static_assert(sizeof(TcEntry) % 16 == 0, "entries move as 16-byte words");
 
 int g_tc_sms = 0;
 int tc_num_sms() {
@@ -267,6 +276,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) mul_tf32x3_kernel(TcArgs a) {
   __shared__ int64_t mC[kTcP];      // C offset of each member's tile origin
   __shared__ int32_t mnj[kTcP];     // row pitch of each member's C block
   __shared__ int32_t swd[kTcS];     // lambda extent staged in each buffer
+  __shared__ __align__(16) TcEntry sent[2][kTcE];  // stage entries, two chunks
   __shared__ int s_panel_ok, s_th, s_mused;
   __shared__ int64_t s_e0, s_ne;
   __shared__ volatile int s_abort;
@@ -283,7 +293,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) mul_tf32x3_kernel(TcArgs a) {
     s_abort = 0;
   }
   if (warp == 0) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 32;\n" ::"r"(tc_smem(&tmem_base)));
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(tc_smem(&tmem_base)),
+                 "n"(kTcCols));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n");
   }
   asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
@@ -291,7 +302,10 @@ __global__ void __launch_bounds__(kTcThreads, 1) mul_tf32x3_kernel(TcArgs a) {
   asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
   const uint32_t tmem = tmem_base;
   const uint32_t sbase = tc_smem(tsm);
-  int64_t g = 0;  // stages this CTA has issued
+  int64_t g = 0;   // stages this CTA has issued
+  int64_t gd = 0;  // stages whose accumulators have been added
+  const int q = warp & 3, h = warp >> 2;  // this warp's TMEM lanes 32q .. and columns 16h ..
+  float acc[16];
 
   for (;;) {
     if (tid == 0) {
@@ -322,6 +336,27 @@ __global__ void __launch_bounds__(kTcThreads, 1) mul_tf32x3_kernel(TcArgs a) {
     if (!s_panel_ok) break;
     const int th = s_th, mused = s_mused;
     const int64_t e0 = s_e0, ne = s_ne;
+#pragma unroll
+    for (int u = 0; u < 16; ++u) acc[u] = 0.0f;
+    // stage k has finished: add its accumulator (rows 32q + lane, columns 16h ..) to acc
+    auto drain = [&](int64_t k) {
+      const int b = (int)(k % kTcS);
+      tc_wait(&mbar[b], (uint32_t)((k / kTcS) & 1), &s_abort, a.err);
+      asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+      if (16 * h < th) {
+        uint32_t v[16];
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, "
+            "[%16];\n"
+            : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+              "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+            : "r"(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(b * kTcN + 16 * h)));
+        asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+#pragma unroll
+        for (int u = 0; u < 16; ++u) acc[u] += __uint_as_float(v[u]);
+      }
+      asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+    };
     const uint32_t idesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)((th <= 16 ? 16 : 32) >> 3) << 17) |
                            ((uint32_t)(kTcM >> 4) << 24);
 
@@ -330,10 +365,20 @@ __global__ void __launch_bounds__(kTcThreads, 1) mul_tf32x3_kernel(TcArgs a) {
         // ---- stage m: copies into buffer (g + m) % kTcS -------------------------------
         const int64_t gm = g + m;
         const int b = (int)(gm % kTcS);
-        if (gm >= kTcS) tc_wait(&mbar[b], (uint32_t)((gm / kTcS - 1) & 1), &s_abort, a.err);
-        const TcEntry* en = a.ent + e0 + m;
-        const int nl = __ldg(&en->nl), wd = __ldg(&en->wd);
-        const int64_t xo = __ldg(&en->x);
+        while (gd <= gm - kTcS) drain(gd++);  // frees buffer b and its accumulator
+        if (m % kTcE == 0) {
+          // entries m .. m + kTcE - 1 of this panel -> chunk (m / kTcE) & 1, which the
+          // threads last read at stages m - 2 kTcE .. m - kTcE - 1 (or in an earlier panel)
+          const int cnt = (int)min((int64_t)kTcE, ne - m);
+          const uint4* src = reinterpret_cast<const uint4*>(a.ent + e0 + m);
+          uint4* dst = reinterpret_cast<uint4*>(sent[(m / kTcE) & 1]);
+          constexpr int kW = (int)(sizeof(TcEntry) / 16);
+          for (int i = tid; i < cnt * kW; i += kTcThreads) dst[i] = __ldg(src + i);
+          __syncthreads();
+        }
+        const TcEntry* en = &sent[(m / kTcE) & 1][m % kTcE];
+        const int nl = en->nl, wd = en->wd;
+        const int64_t xo = en->x;
         if (tid == 0) swd[b] = wd;
         unsigned char* buf = tsm + (size_t)b * kTcBuf;
         const int nkc = (wd + 3) >> 2;         // 16-byte chunks holding data
@@ -344,7 +389,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) mul_tf32x3_kernel(TcArgs a) {
         for (int e = tid; e < mused * nkc; e += kTcThreads) {
           const int r = __float2int_rz(((float)e + 0.5f) * rk), kc = e - r * nkc;
           const int rt = rowtab[r];
-          const int64_t ys = __ldg(&en->y[rt >> 8]);
+          const int64_t ys = en->y[rt >> 8];
           const uint32_t off = (uint32_t)(r >> 3) * kTcSBO + kc * 128 + (r & 7) * 16;
           float* dh = reinterpret_cast<float*>(buf + off);
           float* dl = reinterpret_cast<float*>(buf + kTcAPlane + off);
@@ -407,11 +452,12 @@ __global__ void __launch_bounds__(kTcThreads, 1) mul_tf32x3_kernel(TcArgs a) {
           const int kst = (swd[b] + 7) >> 3;
           const uint32_t ah = sbase + (uint32_t)b * kTcBuf, al = ah + kTcAPlane;
           const uint32_t bh = ah + 2 * kTcAPlane, bl = bh + kTcBPlane;
+          const uint32_t td = tmem + (uint32_t)(b * kTcN);  // this stage's accumulator
           for (int s = 0; s < kst; ++s) {
             const uint32_t o = (uint32_t)s * 256;  // K = 8 tf32 = two 16-byte core matrices
-            tc_mma(tmem, tc_desc(ah + o), tc_desc(bh + o), idesc, (e > 0 || s > 0) ? 1u : 0u);
-            tc_mma(tmem, tc_desc(ah + o), tc_desc(bl + o), idesc, 1u);
-            tc_mma(tmem, tc_desc(al + o), tc_desc(bh + o), idesc, 1u);
+            tc_mma(td, tc_desc(al + o), tc_desc(bh + o), idesc, s > 0 ? 1u : 0u);
+            tc_mma(td, tc_desc(ah + o), tc_desc(bl + o), idesc, 1u);
+            tc_mma(td, tc_desc(ah + o), tc_desc(bh + o), idesc, 1u);
           }
           asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
               tc_smem(&mbar[b])));
@@ -419,24 +465,9 @@ __global__ void __launch_bounds__(kTcThreads, 1) mul_tf32x3_kernel(TcArgs a) {
       }
     }
     g += ne;
-    // ---- epilogue: D (tensor memory) -> C ---------------------------------------------------
-    if (ne > 0) tc_wait(&mbar[(g - 1) % kTcS], (uint32_t)(((g - 1) / kTcS) & 1), &s_abort, a.err);
-    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-    const int q = warp & 3, h = warp >> 2;  // TMEM lanes 32q .., columns 16h ..
+    // ---- epilogue: remaining stage sums, then acc -> C -----------------------------------
+    while (gd < g) drain(gd++);
     if (16 * h < th) {
-      uint32_t v[16];
-      if (ne > 0) {
-        asm volatile(
-            "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, "
-            "[%16];\n"
-            : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
-              "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
-            : "r"(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(16 * h)));
-        asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
-      } else {
-#pragma unroll
-        for (int u = 0; u < 16; ++u) v[u] = 0u;
-      }
       const int mrow = 32 * q + lane;
       if (mrow < mused) {
         const int rt = rowtab[mrow];
@@ -447,17 +478,16 @@ __global__ void __launch_bounds__(kTcThreads, 1) mul_tf32x3_kernel(TcArgs a) {
 #pragma unroll
         for (int u = 0; u < 16; ++u) {
           const int n = 16 * h + u;
-          if (n < th) cp[n * nj] = bad ? __int_as_float(0x7fc00000) : __uint_as_float(v[u]);
+          if (n < th) cp[n * nj] = bad ? __int_as_float(0x7fc00000) : acc[u];
         }
       }
     }
-    asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
     __syncthreads();
   }
   asm volatile("cp.async.wait_all;\n" ::: "memory");
   asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
   __syncthreads();
-  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 32;\n" ::"r"(tmem));
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "n"(kTcCols));
 }
 
 static s_status tc_split(const s_pattern_t* p, bool transpose, const float* x, float* hi, float* lo, cudaStream_t st) {
