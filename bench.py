@@ -469,22 +469,25 @@ def main():
                            "rel_frob_err_vs_fp64": float((Cdf - C64).norm() / C64.norm()),
                            "speedup_vs_fp64": ms64 / msdf}
         del Cdf, plandf
-        # split-bfloat16 tensor-core product (float in and out)
-        planbf = sf.Plan(pat, pat, pat, "bf16x3")
-        planbf.set_symmetric_a(True)
+        # split-bfloat16 (mma.sync) and split-TF32 (tcgen05) tensor-core products, float in and out
         Cbf = torch.empty_like(A32)
-        planbf.mul(A32, A32, Cbf)
-        torch.cuda.synchronize()
-        e0.record(stream)
-        for _ in range(3):
+        for name in ("bf16x3", "tf32x3"):
+            planbf = sf.Plan(pat, pat, pat, name)
+            planbf.set_symmetric_a(True)
             planbf.mul(A32, A32, Cbf)
-        e1.record(stream)
-        torch.cuda.synchronize()
-        msbf = e0.elapsed_time(e1) / 3
-        fp64["bf16x3"] = {"ms": round(msbf, 3), "gflops": flops / (msbf * 1e-3) / 1e9,
+            torch.cuda.synchronize()
+            e0.record(stream)
+            for _ in range(3):
+                planbf.mul(A32, A32, Cbf)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            msbf = e0.elapsed_time(e1) / 3
+            fp64[name] = {"ms": round(msbf, 3), "gflops": flops / (msbf * 1e-3) / 1e9,
                           "rel_frob_err_vs_fp64": float((Cbf.double() - C64).norm() / C64.norm()),
                           "speedup_vs_fp64": ms64 / msbf}
-        del C64, plan64, Cbf, planbf
+            del planbf
+            torch.cuda.empty_cache()
+        del C64, plan64, Cbf
         torch.cuda.empty_cache()
 
     # end to end through the C ABI with host buffers (pinned): every step copies its input A

@@ -1,6 +1,7 @@
 """Parity at the benchmark's full size (N = 2^20 points in [0,1]^3, Matern-1/2, ell = 0.1,
 q = 3, leaf 32, eta = 1.0, tau = 1e-8), in the launch configuration bench.py times: the
-FP64, mixed (compensated float) and split-bfloat16 tensor-core products of the whole pattern on the GPU, compared on a seeded sample of
+FP64, mixed (compensated float), split-bfloat16 and split-TF32 tensor-core products of the whole
+pattern on the GPU, compared on a seeded sample of
 output blocks that the FP64 oracle computes one by one (plus every block of the root's row,
 whose lambda lists are the longest, and the last block).
 
@@ -8,7 +9,9 @@ Tolerances: FP64 within 1e-12 relative Frobenius over the sampled blocks, mixed
 (compensated float) within 1e-6, split-bfloat16 tensor-core products within 5e-6: the
 tensor cores' float accumulation over the 18 k8 steps of a lambda slice loses about 2^-23
 per step (measured 2.2e-6 over the whole product), above the 1e-6 the compensated float
-kernel reaches."""
+kernel reaches.  Split-TF32 (tcgen05) within 5e-6 as well: each stage's accumulator is at most
+nine MMAs deep, but the sums over hundreds of lambda stages are plain float additions
+(measured 2.5e-6 over the whole product)."""
 import os
 
 import numpy as np
@@ -38,14 +41,20 @@ def c2():
     pb = sf.Plan(pat, pat, pat, "bf16x3")
     pb.set_symmetric_a(True)
     pb.mul(A32, A32, Cb)
+    cb = Cb.double().cpu().numpy()
+    del pb
+    pt = sf.Plan(pat, pat, pat, "tf32x3")
+    pt.set_symmetric_a(True)
+    pt.mul(A32, A32, Cb)
     torch.cuda.synchronize()
-    return pat, vals.cpu().numpy(), C64.cpu().numpy(), C32.double().cpu().numpy(), Cb.double().cpu().numpy()
+    return (pat, vals.cpu().numpy(), C64.cpu().numpy(), C32.double().cpu().numpy(), cb,
+            Cb.double().cpu().numpy())
 
 
 def test_fullsize_sampled_parity(c2):
     from oracle import product as oprod
     from oracle.sformat import BlockCSR
-    pat, aval, c64, c32, cb = c2
+    pat, aval, c64, c32, cb, ct = c2
     bo, rp, ci = pat.arrays()
     A = BlockCSR(np.diff(bo), rp, ci.astype(np.int64), aval)
     rng = np.random.Generator(np.random.PCG64(2024))
@@ -58,3 +67,4 @@ def test_fullsize_sampled_parity(c2):
     assert np.linalg.norm(c64[idx] - want) <= 1e-12 * n
     assert np.linalg.norm(c32[idx] - want) <= 1e-6 * n
     assert np.linalg.norm(cb[idx] - want) <= 5e-6 * n
+    assert np.linalg.norm(ct[idx] - want) <= 5e-6 * n
