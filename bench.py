@@ -49,6 +49,9 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--batch", type=int, default=256, help="matrices of the batched workload")
     ap.add_argument("--precisions", default="fp64,fp64_df,mixed", help="drivers mode: arithmetic forms to run")
+    ap.add_argument("--product", choices=["fp32", "tf32x3", "bf16x3"], default="fp32",
+                    help="arithmetic of the timed product: compensated float (default) or a split "
+                         "tensor-core form")
     return ap.parse_args()
 
 
@@ -398,7 +401,7 @@ def main():
     from paper_2211_11681_gb300 import sformat as sf
     b, pat, vals, prep = build_input(w, n)
     t0 = time.time()
-    plan32 = sf.Plan(pat, pat, pat, "fp32")
+    plan32 = sf.Plan(pat, pat, pat, args.product)
     plan32.set_symmetric_a(True)      # A = T K T^T (+ mu I) is symmetric
     triples, flops = plan32.stats()
     prep["plan_s"] = round(time.time() - t0, 2)
@@ -537,25 +540,40 @@ def main():
 
     peaks = measured_peaks()
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
-    fp32_peak = 152 * 128 * 2 * sm_max * 1e6 / 1e12      # TFLOP/s from unit counts and clock
     achieved = flops / (statistics.mean(launch_ms) * 1e-3) / 1e12
+    if args.product == "fp32":
+        fp32_peak = 152 * 128 * 2 * sm_max * 1e6 / 1e12      # TFLOP/s from unit counts and clock
+        roof = {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
+                "frac": achieved / fp32_peak, "traffic": kernel_traffic(),
+                "kernel": "sf::mul_f32_kernel<tile %d, micro %dx%d, transposed A>" % (shape["tile"], *shape["micro"]),
+                "peak_source": "152 SMs x 128 FP32 lanes x 2 flop x sm_max_mhz (derived)"}
+        launches = 1
+    else:
+        # tensor-core forms: useful flops against the dense peak of the operand type (bf16
+        # measured; TF32 as the measured bf16 burst times the nominal TF32 / bf16 ratio 1.1 / 2.25)
+        bf16 = float(peaks.get("bf16_tflops", 1900.0))
+        tpeak = bf16 * (1.1 / 2.25) if args.product == "tf32x3" else bf16
+        roof = {"bound": "tensor", "achieved": achieved, "peak": tpeak, "unit": "TFLOP/s",
+                "frac": achieved / tpeak, "traffic": None,
+                "kernel": "mul_tf32x3_kernel (tcgen05.mma kind::tf32, three products per term)"
+                if args.product == "tf32x3" else "mul_bf16x3_kernel (mma.sync bf16, six products per term)",
+                "peak_source": ("measured bf16 burst x 1.1/2.25 (nominal TF32/bf16), of measured"
+                                if args.product == "tf32x3" else "measured bf16 burst, of measured")}
+        launches = 2                                          # operand split + product
+    dtype = {"fp32": "f32", "tf32x3": "tf32x3", "bf16x3": "bf16x3"}[args.product]
     qbytes = algorithmic_bytes(pat, 4)
     line = {
         "metric": METRIC, "value": value, "unit": "GFLOP/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(ms, 3), "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "vs_baseline": None, "dtype": dtype, "data": "synthetic",
         "config": dict(workload_config(w, n, pat, triples, flops), parallelism="replicas" if world > 1 else "1 GPU",
-                       prep_seconds=prep),
+                       arithmetic=args.product, prep_seconds=prep),
         "hbm_gbs_algorithmic": qbytes / (ms * 1e-3) / 1e9,
         "fp64": fp64,
-        "roofline": {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
-                     "frac": achieved / fp32_peak, "traffic": kernel_traffic(),
-                     "kernel": "sf::mul_f32_kernel<tile %d, micro %dx%d, transposed A>" % (
-                         shape["tile"], *shape["micro"]),
-                     "peak_source": "152 SMs x 128 FP32 lanes x 2 flop x sm_max_mhz (derived)"},
+        "roofline": roof,
         "clocks": clocks,
         "e2e": e2e,
-        "gpu_launches": args.steps,
+        "gpu_launches": args.steps * launches,
     }
     if rank == 0 and world == 1 and not args.no_cpu:
         v, cores, desc, dt = oracle_sample(pat, vals.cpu().numpy(), args.cpu_seconds)
