@@ -113,7 +113,7 @@ s_status s_plan_stats(s_plan plan, int64_t* triples, double* flops);
  * arithmetic (output tile edge, the micro-tile of one lane, for float also the lambda extent
  * of a stage) on the given operands, three launches each after one warm-up, and keeps the
  * fastest for this plan's forward product.  C is overwritten.  *chosen (optional) receives
- * the variant index.  S_FP64 and S_BF16X3 plans have one shape (no-op).
+ * the variant index.  S_FP64, S_BF16X3 and S_TF32X3 plans have one shape (no-op).
  * Synchronises the stream. */
 s_status s_plan_autotune(s_plan plan, const void* A, const void* B, void* C, void* stream, int* chosen);
 /* Selects kernel variant `variant` (0 .. s_plan_num_variants_of(plan)-1) for the plan's
@@ -133,7 +133,9 @@ int s_plan_num_variants_of(s_plan plan);
 s_status s_plan_set_symmetric_a(s_plan plan, int symmetric);
 /* Shape of a variant of the plan's arithmetic (variant < 0: the current one): output tile edge, the
  * micro-tile of one lane, and the largest lambda extent staged at once (consecutive small
- * lambda blocks are packed into one stage up to this extent).  Any output may be NULL. */
+ * lambda blocks are packed into one stage up to this extent).  For an S_TF32X3 plan: 32 rows
+ * of a panel, 128 MMA rows (member columns), 32 MMA columns, lambda extent 24 per stage.
+ * Any output may be NULL. */
 s_status s_plan_variant(s_plan plan, int variant, int* tile, int* micro_rows, int* micro_cols, int* stage_k);
 
 /* C = P_{S_C}(A B): for every block (nu, nu') of S_C,
@@ -141,7 +143,9 @@ s_status s_plan_variant(s_plan plan, int variant, int* tile, int* micro_rows, in
  *                A(nu,lambda) B(lambda,nu');
  * no entry outside S_C is formed.  A, B, C are device value buffers on S_A, S_B, S_C in
  * the plan's element type; C must not alias A or B.  Deterministic: each output entry is
- * summed by one thread in increasing lambda order. */
+ * summed by one thread in increasing lambda order.  S_TF32X3 waits on its own tensor-core
+ * work with a limit of about one second; if that ever runs out, the outputs written from
+ * then on are NaN. */
 s_status s_mul_masked(s_plan plan, const void* A, const void* B, void* C, void* stream);
 
 /* Adjoint of s_mul_masked (reverse mode):  dA = P_{S_A}(dC B^T),  dB = P_{S_B}(A^T dC).
