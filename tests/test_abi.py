@@ -62,3 +62,17 @@ def test_null_arguments_are_rejected():
     assert sf.lib.s_plan_create(None, None, None, 0, None) == sf.S_ERR_ARG
     assert sf.lib.s_pattern_nnz(None) == -1
     assert "s_plan_create" in sf.lib.s_last_error().decode()
+
+
+def test_binding_enums_match_the_header():
+    # the ctypes binding passes plain ints: its precision and status values must be the
+    # header's enumerators
+    from paper_2211_11681_gb300 import sformat as sf
+    text = open(os.path.join(ROOT, "include", "sformat.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    enums = {m.group(1): int(m.group(2)) for m in re.finditer(r"\b(S_[A-Z0-9_]+)\s*=\s*(-?\d+)", text)}
+    for name in ("S_FP64", "S_FP32", "S_BF16X3", "S_FP64_DF", "S_TF32X3", "S_OK", "S_ERR_ARG", "S_ERR_PATTERN",
+                 "S_ERR_MISMATCH"):
+        assert getattr(sf, name) == enums[name], name
+    assert sf.PREC == {"fp64": enums["S_FP64"], "fp32": enums["S_FP32"], "bf16x3": enums["S_BF16X3"],
+                       "fp64_df": enums["S_FP64_DF"], "tf32x3": enums["S_TF32X3"]}
