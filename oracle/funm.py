@@ -13,7 +13,8 @@ Test infrastructure only (see ``oracle/__init__``).
                  to S.  Reading: c = 1.01 * norm_estimate(A), frozen.  Optional residual
                  correction after the iteration (Newton's method for Y^2 = A/c with the
                  inverse of Y replaced by the coupled iterate Z ~ (A/c)^{-1/2}):
-                 R = A/c - P_S(Y Y), Y <- Y + P_S(Z R)/2, repeated `refine` times.
+                 R = A/c - P_S(Y Y), Y <- Y + P_S(Z R)/2, repeated `refine` times
+                 (``ns_refine``).
   expm_taylor    exp(sign * A) by the power series of Sec. 4.4, truncated at degree 8
                  (Sec. 5.3 finds stagnation after 8 terms), evaluated by Horner's rule on
                  X = sign*A/2^s, then s masked squarings.  Reading: s = max(0,
@@ -68,14 +69,22 @@ def sqrtm_ns(A, steps=25, c=None, return_history=False, nthreads=1, refine=0):
         Yn = _prod.mul_masked(Y, T, A, nthreads=nthreads)
         Zn = _prod.mul_masked(T, Z, A, nthreads=nthreads)
         Y, Z = Yn, Zn
-    B = A.like(A.val / c)
-    for _ in range(refine):
-        R = add(B, _prod.mul_masked(Y, Y, A, nthreads=nthreads), 1.0, -1.0)
-        Y = add(Y, _prod.mul_masked(Z, R, A, nthreads=nthreads), 1.0, 0.5)
+    Y = ns_refine(A.like(A.val / c), Y, Z, refine, nthreads=nthreads)
     X = A.like(math.sqrt(c) * Y.val)
     if return_history:
         return X, hist, c
     return X
+
+
+def ns_refine(B, Y, Z, steps, nthreads=1):
+    """Residual correction of an approximate square root Y of B with Z ~ B^{-1/2}: Newton's
+    method for Y^2 = B, the correction E of (Y + E)^2 = B to first order being taken as
+    Z R / 2 with R = B - Y Y (exact when Y, Z and R commute).  Every product masked to B's
+    pattern:  R = B - P_S(Y Y),  Y <- Y + P_S(Z R)/2,  `steps` times."""
+    for _ in range(steps):
+        R = add(B, _prod.mul_masked(Y, Y, B, nthreads=nthreads), 1.0, -1.0)
+        Y = add(Y, _prod.mul_masked(Z, R, B, nthreads=nthreads), 1.0, 0.5)
+    return Y
 
 
 def sqrt_residual(X, A, nthreads=1):

@@ -8,8 +8,12 @@ Layout: clusters are block rows/columns; cluster nu owns rows boff[nu]:boff[nu+1
 of row nu is (nu, colidx[k]) for rowptr[nu] <= k < rowptr[nu+1]; its entries are stored
 row-major at val[voff[k]:voff[k+1]].
 
-Threshold reading: a block is kept iff it is a diagonal block or one of its entries has
-|a| >= tau; entries with |a| < tau inside kept blocks are set to zero.
+Threshold reading (the paper's a-posteriori pattern, Sec. 5, drops entries below tau; the
+store keeps whole blocks): the decision is taken on the unordered pair, so that the kept
+pattern of a symmetric matrix stays symmetric even where T K T^T is symmetric only up to
+rounding.  With m(p, q) = max(|a_pq|, |a_qp|):
+  * block (nu, nu') is kept iff nu = nu' or m >= tau for one of its entries;
+  * entries with m < tau inside kept blocks are set to zero.
 """
 import numpy as np
 
@@ -117,16 +121,19 @@ def compress(Khat, bsize, rowptr, colidx, tau=0.0):
     boff = np.zeros(len(bsize) + 1, dtype=np.int64)
     boff[1:] = np.cumsum(bsize)
     nc = len(bsize)
+    mag = np.abs(np.asarray(Khat, dtype=np.float64))
+    mag = np.maximum(mag, mag.T)                 # m(p, q): the pair decides
     keep_rowptr = np.zeros(nc + 1, dtype=np.int64)
     keep_cols = []
     for i in range(nc):
         for k in range(rowptr[i], rowptr[i + 1]):
             j = colidx[k]
-            blk = Khat[boff[i]:boff[i + 1], boff[j]:boff[j + 1]]
-            if i == j or np.any(np.abs(blk) >= tau):
+            blk = mag[boff[i]:boff[i + 1], boff[j]:boff[j + 1]]
+            if i == j or np.any(blk >= tau):
                 keep_cols.append(j)
         keep_rowptr[i + 1] = len(keep_cols)
     A = BlockCSR.from_dense(Khat, bsize, keep_rowptr, np.array(keep_cols, dtype=np.int64))
     if tau > 0.0:
-        A.val[np.abs(A.val) < tau] = 0.0
+        M = BlockCSR.from_dense(mag, bsize, keep_rowptr, np.array(keep_cols, dtype=np.int64))
+        A.val[M.val < tau] = 0.0
     return A

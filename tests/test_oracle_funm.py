@@ -90,3 +90,55 @@ def test_taylor_degree8_scalar():
     A = BlockCSR(np.array([1]), np.array([0, 1]), np.array([0]), np.array([0.3]))
     E = funm.expm_taylor(A, s=0)
     assert E.val[0] == pytest.approx(sum(0.3 ** k / math.factorial(k) for k in range(9)), rel=1e-15)
+
+
+def _sqrt_and_inverse(B):
+    ev, V = np.linalg.eigh(B.to_dense())
+    return (V * np.sqrt(ev)) @ V.T, (V / np.sqrt(ev)) @ V.T
+
+
+def test_refine_contraction_commuting_perturbation():
+    # Y = (1 + e) S with S = B^{1/2} and Z = S^{-1} exactly: R = B - Y^2 = -(2e + e^2) S^2 and
+    # Y + Z R / 2 = (1 - e^2/2) S, so one correction leaves the relative error e^2/2 and a
+    # second one (e^2/2)^2 / 2 = e^4/8.  A sign slip gives (1 + 2e) S; a lost factor 1/2
+    # gives (1 - e - e^2) S.
+    c = full_case(120, nugget=5e-2)
+    A = c.A
+    B = A.like(A.val / (1.01 * funm.norm_estimate(A)))
+    S, Si = _sqrt_and_inverse(B)
+    eps = 1e-3
+    Y = BlockCSR.from_dense((1 + eps) * S, A.bsize, A.rowptr, A.colidx)
+    Z = BlockCSR.from_dense(Si, A.bsize, A.rowptr, A.colidx)
+    ns = np.linalg.norm(S)
+    Y1 = funm.ns_refine(B, Y, Z, 1)
+    assert np.linalg.norm(Y1.to_dense() - S) / ns == pytest.approx(eps ** 2 / 2, rel=1e-6)
+    Y2 = funm.ns_refine(B, Y, Z, 2)
+    assert np.linalg.norm(Y2.to_dense() - S) / ns < 2e-13 + eps ** 4 / 8 * 1.01
+
+
+def test_refine_one_step_closed_form_general_perturbation():
+    # Y = S + E, Z = S^{-1}: Y + Z (B - Y^2)/2 = S + E/2 - S^{-1} E S / 2 - S^{-1} E^2 / 2
+    # exactly, for any E (the non-commuting part of E survives to first order).
+    c = full_case(100, nugget=5e-2)
+    A = c.A
+    B = A.like(A.val / (1.01 * funm.norm_estimate(A)))
+    S, Si = _sqrt_and_inverse(B)
+    rng = np.random.Generator(np.random.PCG64(11))
+    E = rng.standard_normal(S.shape) * 1e-4 * np.abs(S).max()
+    Y = BlockCSR.from_dense(S + E, A.bsize, A.rowptr, A.colidx)
+    Z = BlockCSR.from_dense(Si, A.bsize, A.rowptr, A.colidx)
+    got = funm.ns_refine(B, Y, Z, 1).to_dense()
+    want = S + E / 2 - Si @ E @ S / 2 - Si @ E @ E / 2
+    np.testing.assert_allclose(got, want, atol=1e-12 * np.abs(S).max())
+
+
+def test_sqrtm_ns_refine_improves_an_unconverged_iteration():
+    # four Newton-Schulz steps leave the full-pattern square root far from converged; the
+    # two double corrections of sqrtm_ns(refine=2) move it towards the eigh square root
+    c = full_case(120, nugget=5e-2)
+    A = c.A
+    ev, V = np.linalg.eigh(A.to_dense())
+    want = (V * np.sqrt(ev)) @ V.T
+    e0 = np.linalg.norm(funm.sqrtm_ns(A, steps=4).to_dense() - want)
+    e2 = np.linalg.norm(funm.sqrtm_ns(A, steps=4, refine=2).to_dense() - want)
+    assert e2 < 0.1 * e0
