@@ -49,6 +49,9 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--batch", type=int, default=256, help="matrices of the batched workload")
     ap.add_argument("--precisions", default="fp64,fp64_df,mixed", help="drivers mode: arithmetic forms to run")
+    ap.add_argument("--tau", type=float, default=None, help="override the workload's threshold")
+    ap.add_argument("--sizes", default="5000,10000,50000,100000,250000,500000,1000000",
+                    help="paper_mult_2d/3d: the N of the sweep")
     ap.add_argument("--product", choices=["fp32", "tf32x3", "bf16x3"], default="fp32",
                     help="arithmetic of the timed product: compensated float (default) or a split "
                          "tensor-core form")
@@ -140,11 +143,11 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(mine)}
 
 
-def kernel_traffic():
+def kernel_traffic(record="mul_f32_nt_traffic.json", source="mul_nt.cu"):
     """Per-launch DRAM bytes of the product kernel from the committed ncu summary, if it
     was taken on the current kernel source; else None."""
-    path = os.path.join(ROOT, "profiles", "mul_f32_traffic.json")
-    src = os.path.join(ROOT, "paper_2211_11681_gb300", "csrc", "mul.cu")
+    path = os.path.join(ROOT, "profiles", record)
+    src = os.path.join(ROOT, "paper_2211_11681_gb300", "csrc", source)
     try:
         with open(path) as f:
             rec = json.load(f)
@@ -310,6 +313,150 @@ def run_batch(args, rank, world):
         print(json.dumps(line), flush=True)
 
 
+def run_paper_mult(args, rank, world):
+    """The multiplication benchmark of Sec. 5.1: K (.) K~ with K the compressed exponential
+    kernel exp(-r)/N (q+1 = 4 vanishing moments, eta = 1.25, tau = 1e-5/N) on uniform points
+    in [0,1]^d and K~ = K (1 + 0.1 u); the formatted product on K's a-posteriori pattern in
+    FP64 and in compensated float, timed, and its error e_F(K K~ - K (.) K~) = ||(..) X||_F /
+    ||X||_F with X in R^{N x 10} uniform.  One JSON line per N, then a summary line."""
+    import torch
+    import workloads as W
+    from paper_2211_11681_gb300 import sformat as sf
+    from paper_2211_11681_gb300.builder import Builder
+    w = W.WORKLOADS[args.workload]
+    ns = [args.n] if args.n else [int(v) for v in args.sizes.split(",")]
+    stream = torch.cuda.current_stream()
+    rows = []
+
+    def timed(fn, reps):
+        fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    for n in ns:
+        t0 = time.time()
+        x = W.points(w, n)
+        b = Builder(x, w.leaf, w.q, w.eta)
+        pat, K = b.values(w.nu, w.ell, 1.0 / n, w.nugget, W.tau_of(w, n))
+        apriori = b.nnz_apriori
+        del b
+        prep = time.time() - t0
+        g = torch.Generator(device="cuda")
+        g.manual_seed(w.seed + 100)
+        Kt = K * (1.0 + 0.1 * torch.rand(K.numel(), dtype=torch.float64, device="cuda", generator=g))
+        g.manual_seed(99)
+        X = torch.rand((10, n), dtype=torch.float64, device="cuda", generator=g)
+        p64 = sf.Plan(pat, pat, pat, "fp64")
+        triples, flops = p64.stats()
+        C64 = torch.empty_like(K)
+        ms64 = timed(lambda: p64.mul(K, Kt, C64), 1 if flops > 2e12 else 3)
+        T1, T2, T3 = (torch.empty_like(X) for _ in range(3))
+        sf.spmm(pat, Kt, X, T1)
+        sf.spmm(pat, K, T1, T2)                      # K (K~ X): the exact product applied to X
+        sf.spmm(pat, C64, X, T3)
+        xn = float(X.norm())
+        ef64 = float((T2 - T3).norm()) / xn
+        del p64
+        K32, Kt32 = K.float(), Kt.float()
+        C32 = torch.empty_like(K32)
+        p32 = sf.Plan(pat, pat, pat, "fp32")
+        shape = p32.autotune(K32, Kt32, C32)
+        ms32 = timed(lambda: p32.mul(K32, Kt32, C32), 3)
+        C32d = C32.double()
+        sf.spmm(pat, C32d, X, T3)
+        ef32 = float((T2 - T3).norm()) / xn
+        rel32 = float((C32d - C64).norm() / C64.norm())
+        row = {"n": n, "d": w.d, "apriori_nnz": apriori, "nnz": pat.nnz, "blocks": pat.nblocks, "triples": triples,
+               "flops": flops, "prep_s": round(prep, 2),
+               "fp64": {"ms": round(ms64, 3), "tflops": flops / ms64 / 1e9, "e_F": ef64},
+               "f32": {"ms": round(ms32, 3), "tflops": flops / ms32 / 1e9, "e_F": ef32, "rel_frob_vs_fp64": rel32,
+                       "shape": shape},
+               "norm_KKtX": float(T2.norm()) / xn}
+        rows.append(row)
+        if rank == 0:
+            print(json.dumps({"paper_mult_point": row}), flush=True)
+        del K, Kt, K32, Kt32, C32, C32d, C64, X, T1, T2, T3, p32, pat
+        torch.cuda.empty_cache()
+    line = {"metric": "formatted product K (.) K~ on the a-posteriori pattern (Sec. 5.1): ms, TFLOP/s, e_F",
+            "value": rows[-1]["f32"]["ms"], "unit": "ms per product (float, largest N)", "higher_is_better": False,
+            "n_gpus": world, "dtype": "f32+f64", "data": "synthetic",
+            "config": {"workload": w.name, "d": w.d, "kernel": "exp(-r)/N (Matern-1/2, ell=1)", "q": w.q,
+                       "eta": w.eta, "tau": "1e-5/N", "leaf": w.leaf, "perturbation": "K~ = K (1 + 0.1 u), u ~ U[0,1]",
+                       "estimator": "e_F(M) = ||M X||_F/||X||_F, X in R^{N x 10} uniform [0,1]"},
+            "points": rows,
+            "paper_context": "Sec. 5.1 plots e_F between 1e-8 and 2e-6 for N = 5e3..1e6 (point values not in the source)"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+def run_grad(args, rank, world):
+    """Differentiation through k Newton-Schulz steps (uniform [0,1]^3, Matern-3/2, ell = 0.15,
+    q = 2, eta = 1.25): L(ell) = z^T P_S(A(ell)^{1/2}) z with z = T g, g ~ N(0, I), the
+    mixed-precision iteration (float, float checkpoints) differentiated in float
+    (s_funm_sqrt_backward_prec) under torch.autograd, then dL/dell = <dL/dA, dA/dell> with
+    dA/dell = P_S(T dK/dell T^T) from the builder.  Reports the time and device memory of the
+    forward and reverse passes, and the same in double when --precisions holds fp64."""
+    import torch
+    import workloads as W
+    from paper_2211_11681_gb300 import sformat as sf
+    from paper_2211_11681_gb300.autograd import QuadForm, SqrtmNS
+    from paper_2211_11681_gb300.builder import Builder
+    w = W.WORKLOADS["matern32_3d_grad"]
+    n = args.n or w.n
+    steps = 10
+    tau = args.tau if args.tau is not None else w.tau
+    t0 = time.time()
+    x = W.points(w, n)
+    b = Builder(x, w.leaf, w.q, w.eta)
+    pat, A = b.values(w.nu, w.ell, 1.0 / n, w.nugget, tau)
+    dAdl = b.values_dell(pat, w.nu, w.ell, 1.0 / n)
+    z = torch.from_numpy(b.transform(W.random_vector(n, 17))).cuda()
+    apriori = b.nnz_apriori
+    del b
+    prep = time.time() - t0
+    lam = sf.norm_est(pat, A, 50)
+    c = 1.01 * lam
+    free0, total = torch.cuda.mem_get_info()
+    out = {}
+    for prec in [p_ for p_ in args.precisions.split(",") if p_ in ("fp32", "fp64")]:
+        torch.cuda.synchronize()
+        Ar = A.clone().requires_grad_(True)
+        t1 = time.time()
+        X = SqrtmNS.apply(Ar, pat, steps, c, prec)
+        L = QuadForm.apply(X, pat, z)
+        torch.cuda.synchronize()
+        t2 = time.time()
+        free1, _ = torch.cuda.mem_get_info()
+        L.backward()
+        torch.cuda.synchronize()
+        t3 = time.time()
+        dl = float(torch.dot(Ar.grad, dAdl))
+        out[prec] = {"loss": float(L.detach()), "dloss_dell": dl, "forward_s": round(t2 - t1, 3),
+                     "backward_s": round(t3 - t2, 3),
+                     "device_gb_in_use_after_forward": round((total - free1) / 1e9, 2),
+                     "checkpoint_gb": round(2 * steps * pat.nnz * (4 if prec == "fp32" else 8) / 1e9, 2)}
+        del Ar, X, L
+        torch.cuda.empty_cache()
+    if "fp32" in out and "fp64" in out:
+        out["fp32"]["dloss_dell_rel_vs_fp64"] = abs(out["fp32"]["dloss_dell"] / out["fp64"]["dloss_dell"] - 1)
+    line = {"metric": "d/dell of z^T P_S(A(ell)^{1/2}) z through %d Newton-Schulz steps" % steps,
+            "value": out.get("fp32", {}).get("backward_s"), "unit": "s per reverse pass (mixed)",
+            "higher_is_better": False, "n_gpus": world, "dtype": "f32 (+f64 comparison)", "data": "synthetic",
+            "config": {"workload": w.name, "n": n, "d": w.d, "kernel": "matern-1.5", "ell": w.ell, "q": w.q,
+                       "eta": w.eta, "tau": tau, "apriori_nnz": apriori, "nnz": pat.nnz, "blocks": pat.nblocks,
+                       "lambda_max": lam, "c": c, "prep_seconds": round(prep, 1),
+                       "device_gb_in_use_before": round((total - free0) / 1e9, 2)},
+            "grad": out}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
 def run_drivers(args, rank, world):
     """Matrix functions at full size (N = 2^18 points on the sphere, Matern-5/2, ell = 0.3,
     nugget 1e-2, q = 2, eta = 1.25): A^{1/2} by 25 Newton-Schulz steps and exp(-A) by
@@ -383,6 +530,18 @@ def main():
             dist.barrier()
             dist.destroy_process_group()
         return
+    if args.workload == "matern32_3d_grad":
+        run_grad(args, rank, world)
+        if dist is not None:
+            dist.barrier()
+            dist.destroy_process_group()
+        return
+    if args.workload.startswith("paper_mult"):
+        run_paper_mult(args, rank, world)
+        if dist is not None:
+            dist.barrier()
+            dist.destroy_process_group()
+        return
     if args.workload == "matern32_2d_batch":
         run_batch(args, rank, world)
         if dist is not None:
@@ -451,10 +610,11 @@ def main():
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        plan64.mul(vals, vals, C64)
+        for _ in range(3):
+            plan64.mul(vals, vals, C64)
         e1.record(stream)
         torch.cuda.synchronize()
-        ms64 = e0.elapsed_time(e1)
+        ms64 = e0.elapsed_time(e1) / 3
         err = float((C32.double() - C64).norm() / C64.norm())
         fp64 = {"ms": round(ms64, 3), "gflops": flops / (ms64 * 1e-3) / 1e9,
                 "mixed_rel_frob_err_vs_fp64": err, "mixed_speedup_vs_fp64": ms64 / ms}
@@ -464,10 +624,11 @@ def main():
         plandf.mul(vals, vals, Cdf)
         torch.cuda.synchronize()
         e0.record(stream)
-        plandf.mul(vals, vals, Cdf)
+        for _ in range(3):
+            plandf.mul(vals, vals, Cdf)
         e1.record(stream)
         torch.cuda.synchronize()
-        msdf = e0.elapsed_time(e1)
+        msdf = e0.elapsed_time(e1) / 3
         fp64["fp64_df"] = {"ms": round(msdf, 3), "gflops": flops / (msdf * 1e-3) / 1e9,
                            "rel_frob_err_vs_fp64": float((Cdf - C64).norm() / C64.norm()),
                            "speedup_vs_fp64": ms64 / msdf}
@@ -503,7 +664,7 @@ def main():
     Ad = [torch.empty_like(A32) for _ in range(2)]
     Cd = [C32, torch.empty_like(A32)]
     s_h2d, s_d2h = torch.cuda.Stream(), torch.cuda.Stream()
-    e2e_steps = max(2, min(args.steps, 4))
+    e2e_steps = max(2, args.steps)
     ev = lambda: torch.cuda.Event()
     up = [ev() for _ in range(e2e_steps)]
     done = [ev() for _ in range(e2e_steps)]
@@ -541,12 +702,18 @@ def main():
     peaks = measured_peaks()
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
     achieved = flops / (statistics.mean(launch_ms) * 1e-3) / 1e12
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
     if args.product == "fp32":
-        fp32_peak = 152 * 128 * 2 * sm_max * 1e6 / 1e12      # TFLOP/s from unit counts and clock
+        fp32_peak = sms * 128 * 2 * sm_max * 1e6 / 1e12      # TFLOP/s from unit counts and clock
+        nt = tuple(shape["micro"]) == (0, 0)
         roof = {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
-                "frac": achieved / fp32_peak, "traffic": kernel_traffic(),
-                "kernel": "sf::mul_f32_kernel<tile %d, micro %dx%d, transposed A>" % (shape["tile"], *shape["micro"]),
-                "peak_source": "152 SMs x 128 FP32 lanes x 2 flop x sm_max_mhz (derived)"}
+                "frac": achieved / fp32_peak,
+                "traffic": kernel_traffic() if nt else kernel_traffic("mul_f32_traffic.json", "mul.cu"),
+                "kernel": "sf::mul_f32_nt_kernel (K-major operands, one bulk copy per lambda block, "
+                          "split-K half-warps)" if nt else
+                          "sf::mul_f32_kernel<tile %d, micro %dx%d, transposed A>" % (shape["tile"], *shape["micro"]),
+                "peak_source": "%d SMs (device attribute) x 128 FP32 lanes x 2 flop x %g MHz sm_max (derived)"
+                               % (sms, sm_max)}
         launches = 1
     else:
         # tensor-core forms: useful flops against the dense peak of the operand type (bf16

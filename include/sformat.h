@@ -55,7 +55,13 @@ typedef enum {
  *   S_FP64_DF  double in, double out; each operand split into a pair of floats
  *              (hi + lo) and the products formed in float-pair arithmetic with float
  *              error-free transformations; about 2^-44 relative per operation.
- *   S_FP32     float in, float out, float multiply-add.
+ *   S_FP32     float in, float out, float multiply-add; the partial sum of each few lambda
+ *              blocks is folded into the running sum by an error-free two-sum (compensated
+ *              summation over lambda).  The default kernel reads both operands K-major: A as
+ *              stored and B through a padded copy of its transposed blocks that the plan keeps
+ *              (s_pattern_nnz(S_B) floats, rounded up per block to multiples of 4 in each
+ *              dimension), unless s_plan_set_symmetric_a was set and the product is called
+ *              with B = A on one pattern whose block sizes are multiples of 4.
  *   S_BF16X3   float in, float out; each operand split into three bfloat16 parts,
  *              the six leading cross products on the tensor cores, float accumulate.
  *   S_TF32X3   float in, float out; each operand split as hi + lo, both rounded to TF32
@@ -130,11 +136,16 @@ int s_plan_num_variants_of(s_plan plan);
  * caller's promise.  symmetric = 0 restores the default.  For an S_TF32X3 plan the flag
  * needs B's pattern to be A's and the product to be called with B = A (the same buffer);
  * the kernel then reads B(lambda, nu') through the stored block (nu', lambda) and both
- * operands from one set of split planes. */
+ * operands from one set of split planes.  For an S_FP32 plan whose B pattern is A's, the
+ * K-major kernel then reads B(lambda, nu') through the stored (nu', lambda) when called with
+ * B = A (no transposed copy; the plan releases it), and falls back to the other kernel shape
+ * of its tile list when called with another B. */
 s_status s_plan_set_symmetric_a(s_plan plan, int symmetric);
 /* Shape of a variant of the plan's arithmetic (variant < 0: the current one): output tile edge, the
  * micro-tile of one lane, and the largest lambda extent staged at once (consecutive small
- * lambda blocks are packed into one stage up to this extent).  For an S_TF32X3 plan: 32 rows
+ * lambda blocks are packed into one stage up to this extent).  Float variant 0 (the default)
+ * is the K-major kernel: each lambda block staged by one bulk copy, the micro-tile a quarter
+ * of each tile's padded edge (reported as 0 x 0), lambda staged in pieces of at most 20.  For an S_TF32X3 plan: 32 rows
  * of a panel, 128 MMA rows (member columns), 32 MMA columns, lambda extent 24 per stage.
  * Any output may be NULL. */
 s_status s_plan_variant(s_plan plan, int variant, int* tile, int* micro_rows, int* micro_cols, int* stage_k);
@@ -144,10 +155,25 @@ s_status s_plan_variant(s_plan plan, int variant, int* tile, int* micro_rows, in
  *                A(nu,lambda) B(lambda,nu');
  * no entry outside S_C is formed.  A, B, C are device value buffers on S_A, S_B, S_C in
  * the plan's element type; C must not alias A or B.  Deterministic: each output entry is
- * summed by one thread in increasing lambda order.  S_TF32X3 waits on its own tensor-core
- * work with a limit of about one second; if that ever runs out, the outputs written from
- * then on are NaN. */
+ * summed in a fixed order, so the same inputs give the same bits.  S_TF32X3
+ * waits on its own tensor-core work and the K-major S_FP32 kernel on its own bulk copies,
+ * each with a limit of about one second; if that ever runs out, the outputs are unspecified
+ * (NaN where written after the time-out) and the plan records the time-out: the plan's next
+ * s_mul_masked, s_graph_launch or s_plan_status returns S_ERR_TIMEOUT (launching nothing)
+ * and clears the record. */
 s_status s_mul_masked(s_plan plan, const void* A, const void* B, void* C, void* stream);
+
+/* Synchronises `stream`, then reports the plan's device-side record: S_ERR_TIMEOUT (and the
+ * record cleared) if a bounded wait of an earlier product or adjoint of this plan ran out,
+ * else S_OK.  The kernels that wait on the device are the S_TF32X3 kernel (its tensor-core
+ * work) and the K-major S_FP32 kernel (its bulk copies); the others never set the record. */
+s_status s_plan_status(s_plan plan, void* stream);
+/* Diagnostics: *word receives the host address of the plan's forward time-out word (pinned
+ * host memory mapped into the device, 0 = no time-out).  A kernel stores 1 there when its
+ * wait runs out; writing 1 from the host plants a time-out record, which is how the status
+ * path is tested without making a device wait run out.  The word belongs to the plan (valid
+ * until s_plan_destroy). */
+s_status s_plan_timeout_word(s_plan plan, unsigned int** word);
 
 /* Adjoint of s_mul_masked (reverse mode):  dA = P_{S_A}(dC B^T),  dB = P_{S_B}(A^T dC).
  * Either output may be NULL to skip it.  Same element type as the plan. */
@@ -169,6 +195,13 @@ s_status s_graph_destroy(s_graph g);
  * double (S_FP64) or float (S_FP32) buffers.  C may alias A or B. */
 s_status s_add(s_pattern p, s_prec prec, double alpha, const void* A, double beta, const void* B, double gamma,
                void* C, void* stream);
+
+/* Block-sparse times dense: Y = A X for `nvec` vectors, X and Y stored one vector after the
+ * other (N x nvec, column-major, N = the pattern's dimension), double device buffers; Y must
+ * not alias X.  With X an N x 10 matrix of uniform random entries this evaluates the error
+ * estimator e_F(M) = ||M X||_F / ||X||_F of the multiplication benchmark (Sec. 5.1) for
+ * M = A B - P_S(A B) as A (B X) - C X without forming M.  Asynchronous on the stream. */
+s_status s_spmm(s_pattern p, const double* A, const double* X, int nvec, double* Y, void* stream);
 
 /* ---- norm estimate and matrix functions ---------------------------------------------- */
 
@@ -200,8 +233,8 @@ typedef struct {
                          S_EXP*: lambda used for the squaring count (0 = norm estimate)     */
   int squarings;      /* S_EXP*: -1 = from lambda, else forced count                        */
   double* residual;   /* optional host out: S_SQRT residual ||P_S(X X) - A||_F / ||A||_F    */
-  void* checkpoints;  /* optional device buffer of 2*steps*nnz doubles: (Y_k, Z_k) per step
-                         (S_FP64 only)                                                      */
+  void* checkpoints;  /* optional device buffer of 2*steps*nnz iterates: (Y_k, Z_k) per step,
+                         doubles for S_FP64 and S_FP64_DF, floats for S_FP32                */
   int refine;         /* S_SQRT: residual-correction steps in double after the iteration:
                          R = A/c - P_S(Y Y), Y <- Y + P_S(Z R)/2 (Newton's method for
                          Y^2 = A/c with Z standing in for Y^{-1}); 0 = none               */
@@ -231,6 +264,17 @@ s_status s_funm(s_pattern p, s_fn fn, const double* A, double* F, const s_funm_o
  * buffers; prec S_FP64.  Allocates its work buffers; synchronises the stream. */
 s_status s_funm_sqrt_backward(s_pattern p, int steps, double c, const double* checkpoints, const double* dF,
                               double* dA, void* stream);
+
+/* The same reverse mode for the iteration run in another arithmetic: prec S_FP64 is
+ * s_funm_sqrt_backward; prec S_FP32 differentiates the float iteration of s_funm with prec
+ * S_FP32 (its residual corrections, a small change of the result, are not differentiated):
+ * `checkpoints` holds 2*steps*nnz floats written by that s_funm call, every adjoint product
+ * is a compensated-float masked product (S_FP32 plans) and the adjoint iterates are float;
+ * dF and dA are double.  About half the memory and a fraction of the time of the double
+ * form, at float accuracy (relative error of dA near 1e-6).  Allocates its work buffers;
+ * synchronises the stream. */
+s_status s_funm_sqrt_backward_prec(s_pattern p, s_prec prec, int steps, double c, const void* checkpoints,
+                                   const double* dF, double* dA, void* stream);
 
 /* Loss of the differentiation checks: *out (host) = z^T X z = sum over the blocks (nu, nu') of
  * the pattern of z_nu^T X(nu, nu') z_nu', with z a device vector of the pattern's dimension in

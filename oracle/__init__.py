@@ -22,6 +22,7 @@ Modules and the passage of the paper each one follows:
             coupled Newton-Schulz square root, Taylor scaling-and-squaring exponential
             (the power series of Sec. 4.4 with squaring added).
   adjoint   reverse mode of the masked product and of the Newton-Schulz iteration.
+  estimators  the error estimator e_F of the multiplication benchmark (Sec. 5.1).
 
 Every function with no independent pin says "parity unpinned" in its docstring.  At the
 time of writing every function is pinned by a test under ``tests/test_oracle_*.py``.

@@ -2,9 +2,14 @@
 forward and backward step runs in libsformat.so).
 
     MaskedMul.apply(A, B, plan)            C = P_{S_C}(A B); backward by s_mul_masked_adjoint
-    SqrtmNS.apply(A, pattern, steps, c)    A^{1/2} by coupled Newton-Schulz with per-step
+    SqrtmNS.apply(A, pattern, steps, c, prec, refine)
+                                           A^{1/2} by coupled Newton-Schulz with per-step
                                            checkpoints (Y_k, Z_k); backward by
-                                           s_funm_sqrt_backward with c frozen
+                                           s_funm_sqrt_backward_prec with c frozen.
+                                           prec "fp64": double iteration and reverse mode;
+                                           "fp32": float iteration with `refine` double
+                                           residual corrections, float checkpoints, float
+                                           reverse mode
     QuadForm.apply(X, pattern, z)          z^T X z over the pattern's blocks
 """
 import torch
@@ -32,21 +37,26 @@ class MaskedMul(torch.autograd.Function):
 
 class SqrtmNS(torch.autograd.Function):
     @staticmethod
-    def forward(ctx, A, pattern, steps, c):
+    def forward(ctx, A, pattern, steps, c, prec="fp64", refine=0):
+        if c is None or c <= 0:
+            # resolve the automatic scale here, so that backward differentiates the same
+            # iteration with the same frozen c
+            c = 1.01 * sf.norm_est(pattern, A.contiguous(), 50)
         nnz = pattern.nnz
-        ck = torch.empty(2 * steps * nnz + 1, dtype=torch.float64, device=A.device)
+        ck = torch.empty(2 * steps * nnz + 4, dtype=torch.float32 if prec == "fp32" else torch.float64,
+                         device=A.device)
         F = torch.empty_like(A)
-        sf.funm(pattern, "sqrt", A.contiguous(), F, steps=steps, scale=c, checkpoints=ck)
+        sf.funm(pattern, "sqrt", A.contiguous(), F, steps=steps, scale=c, checkpoints=ck, prec=prec, refine=refine)
         ctx.save_for_backward(ck)
-        ctx.pattern, ctx.steps, ctx.c = pattern, steps, c
+        ctx.pattern, ctx.steps, ctx.c, ctx.prec = pattern, steps, c, prec
         return F
 
     @staticmethod
     def backward(ctx, dF):
         (ck,) = ctx.saved_tensors
         dA = torch.empty_like(dF)
-        sf.sqrt_backward(ctx.pattern, ctx.steps, ctx.c, ck, dF.contiguous(), dA)
-        return dA, None, None, None
+        sf.sqrt_backward(ctx.pattern, ctx.steps, ctx.c, ck, dF.contiguous(), dA, prec=ctx.prec)
+        return dA, None, None, None, None, None
 
 
 class QuadForm(torch.autograd.Function):

@@ -42,6 +42,10 @@ class _Borrowed:
     def nblocks(self):
         return int(lib.s_pattern_nblocks(self.h))
 
+    @property
+    def n(self):
+        return _sf.pattern_dim(self.h)
+
     def block_offsets(self):
         out = np.zeros(self.nblocks + 1, dtype=np.int64)
         _sf.check(lib.s_pattern_block_offsets(self.h, out.ctypes.data_as(_P(_i64))))

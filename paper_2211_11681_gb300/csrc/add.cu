@@ -30,10 +30,7 @@ __global__ void add_diag_kernel(int32_t nc, const int32_t* diag, const int32_t* 
 }
 
 static int grid_for(int64_t n) {
-  int dev = 0, sms = 0;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  return (int)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, (int64_t)sms * 8));
+  return (int)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, (int64_t)sm_count() * 8));
 }
 
 s_status run_add(const s_pattern_t* p, s_prec prec, double alpha, const void* A, double beta, const void* B,
@@ -98,6 +95,17 @@ s_status run_spmv_f64(const s_pattern_t* p, const double* A, const double* x, do
 }  // namespace sf
 
 using namespace sf;
+
+extern "C" s_status s_spmm(s_pattern p, const double* A, const double* X, int nvec, double* Y, void* stream) {
+  if (!p || !A || !X || !Y || nvec < 0) return set_error(S_ERR_ARG, "s_spmm: bad argument");
+  if (X == Y) return set_error(S_ERR_ARG, "s_spmm: Y aliases X");
+  const int64_t n = p->d.n;
+  for (int j = 0; j < nvec && n > 0; ++j) {
+    s_status st = run_spmv_f64(p, A, X + (int64_t)j * n, Y + (int64_t)j * n, (cudaStream_t)stream);
+    if (st) return st;
+  }
+  return S_OK;
+}
 
 extern "C" s_status s_add(s_pattern p, s_prec prec, double alpha, const void* A, double beta, const void* B,
                           double gamma, void* C, void* stream) {

@@ -13,6 +13,8 @@ namespace sf {
 // Thread-local error message; set_error returns the status for `return set_error(...)`.
 s_status set_error(s_status st, const std::string& msg);
 s_status cuda_error(cudaError_t e, const char* what);
+// SM count of the current device (cached per device ordinal).
+int sm_count();
 
 #define SF_CUDA(call)                                     \
   do {                                                    \
@@ -88,6 +90,23 @@ struct TcEntry {
   int32_t nl, wd;
 };
 
+// One operand side of the K-major float product (mul_nt.cu): the op(X) row lists or op(Y)
+// column lists, and where the kernel finds each block's K-major slice data: directly in the
+// caller's buffer (offsets = the pattern's voff) or in a padded, per-block transposed copy
+// written by a pre-pass into `scratch` (offsets poff).
+struct NtSideDesc {
+  const int64_t* ptr = nullptr;
+  const int32_t* idx = nullptr;
+  const int32_t* blk = nullptr;
+  const int64_t* off = nullptr;   // nullptr: side not configured
+  const s_pattern_t* pat = nullptr;
+  bool prep = false;              // true: the kernel reads `scratch`
+  bool trans = false;             // prepared copy holds the stored blocks transposed
+  int64_t* poff = nullptr;
+  float* scratch = nullptr;
+  int64_t len = 0;
+};
+
 struct MulDesc {
   Side x, y;                 // C = op(X) op(Y) on S_C
   const s_pattern_t* pc;
@@ -108,8 +127,12 @@ struct MulDesc {
   float* tc_xl = nullptr;
   float* tc_yh = nullptr;
   float* tc_yl = nullptr;
-  unsigned int* tc_err = nullptr;  // set when a bounded wait of the kernel ran out
+  unsigned int* err = nullptr;       // time-out word, device view: set to 1 when a bounded wait
+  unsigned int* err_host = nullptr;  // of a kernel ran out; pinned host memory mapped into the
+                                     // device, so the host reads it without a sync
   bool tc_sym = false;             // symmetric plan: B = A, Y read through its stored transpose
+  NtSideDesc ntx, nty;             // K-major float product sides (S_FP32)
+  bool nt_ysym = false;            // Y side read through X's rows (B = A, symmetric)
   float2* df_x = nullptr;    // S_FP64_DF: split operands (hi, lo)
   float2* df_y = nullptr;
   struct __nv_bfloat16* bf_x = nullptr;  // S_BF16X3: three bfloat16 planes per operand
@@ -125,6 +148,14 @@ void free_desc(MulDesc* d);
 s_status tc_prepare(MulDesc* d);
 void tc_free(MulDesc* d);
 s_status launch_tc(const MulDesc& d, const void* X, const void* Y, void* C, cudaStream_t st);
+// S_ERR_TIMEOUT (and the record cleared) if the descriptor's time-out word is set, else S_OK.
+s_status take_timeout(const MulDesc& d);
+// K-major float product (mul_nt.cu): configure the sides of a float descriptor, whether a call
+// with these buffers can use it, the launch, and the release of its scratch.
+s_status nt_configure(MulDesc* d, bool x_trans, bool y_trans, bool y_sym);
+bool nt_usable(const MulDesc& d, const void* X, const void* Y);
+s_status launch_nt(const MulDesc& d, const void* X, const void* Y, void* C, cudaStream_t st, bool unroll);
+void nt_free_side(NtSideDesc* s);
 s_status run_mul(const MulDesc& d, s_prec prec, const void* X, const void* Y, void* C, cudaStream_t st);
 
 // Element-wise kernels (add.cu)

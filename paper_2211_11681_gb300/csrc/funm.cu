@@ -204,10 +204,10 @@ extern "C" s_status s_funm(s_pattern p, s_fn fn, const double* A, double* F, con
     if ((s = run_add(p, aprec, 1.0, Z, 0.0, nullptr, 1.0, Z, st))) return s;
     const int refine = std::max(0, o.refine);
     for (int k = 0; k < steps; ++k) {
-      if (o.checkpoints && aprec == S_FP64) {
-        double* ck = (double*)o.checkpoints + (int64_t)2 * k * nnz;
+      if (o.checkpoints) {  // (Y_k, Z_k) in the iterates' element type
+        char* ck = (char*)o.checkpoints + (int64_t)2 * k * nnz * (int64_t)w;
         SF_CUDA(cudaMemcpyAsync(ck, Y, w * nnz, cudaMemcpyDeviceToDevice, st));
-        SF_CUDA(cudaMemcpyAsync(ck + nnz, Z, w * nnz, cudaMemcpyDeviceToDevice, st));
+        SF_CUDA(cudaMemcpyAsync(ck + (int64_t)nnz * w, Z, w * nnz, cudaMemcpyDeviceToDevice, st));
       }
       if ((s = run_mul(plan->fwd, prec, Z, Y, P, st))) return s;                 // P = P_S(Z Y)
       if ((s = run_add(p, aprec, -0.5, P, 0.0, nullptr, 1.5, T, st))) return s;   // T = (3I - P)/2
@@ -271,6 +271,7 @@ extern "C" s_status s_funm(s_pattern p, s_fn fn, const double* A, double* F, con
           return set_error(S_ERR_NOT_CONVERGED, "s_funm: Newton-Schulz iteration diverged at step " + std::to_string(k));
       }
     }
+    if ((s = s_plan_status(plan, st))) return s;
     if (o.residual) {
       // ||P_S(F F) - A||_F / ||A||_F in double
       s_plan p64 = nullptr;
@@ -351,49 +352,78 @@ extern "C" s_status s_funm(s_pattern p, s_fn fn, const double* A, double* F, con
   return set_error(S_ERR_ARG, "s_funm: unknown function");
 }
 
-extern "C" s_status s_funm_sqrt_backward(s_pattern p, int steps, double c, const double* ck, const double* dF,
-                                         double* dA, void* stream) {
-  if (!p || !ck || !dF || !dA || steps < 1 || !(c > 0.0)) return set_error(S_ERR_ARG, "s_funm_sqrt_backward: bad argument");
-  if (!p->has_all_diag) return set_error(S_ERR_PATTERN, "s_funm_sqrt_backward: the pattern must hold every diagonal block");
-  cudaStream_t st = (cudaStream_t)stream;
+// Reverse mode of the coupled Newton-Schulz iteration of s_funm(S_SQRT) with c frozen, in
+// double (prec S_FP64: double checkpoints, double adjoint products) or in float (prec S_FP32:
+// float checkpoints, compensated-float adjoint products, float adjoint iterates; dF and dA
+// stay double).
+static s_status sqrt_backward(s_pattern p, s_prec prec, int steps, double c, const void* ck, const double* dF,
+                              double* dA, cudaStream_t st) {
   const int64_t nnz = p->d.nnz;
+  const size_t w = prec == S_FP32 ? sizeof(float) : sizeof(double);
   s_plan plan = nullptr;
-  s_status s = s_plan_create(p, p, p, S_FP64, &plan);
+  s_status s = s_plan_create(p, p, p, prec, &plan);
   if (s) return s;
   struct PlanGuard {
     s_plan q;
     ~PlanGuard() { s_plan_destroy(q); }
   } pg{plan};
-  const size_t bytes = sizeof(double) * nnz + 16;
+  const size_t bytes = w * nnz + 16;
   DevBuf b[10];
   for (auto& x : b) SF_CUDA(cudaMalloc(&x.p, bytes));
   SyncOnExit sync{st};
-  double *dY = (double*)b[0].p, *dZ = (double*)b[1].p, *P = (double*)b[2].p, *T = (double*)b[3].p;
-  double *dYa = (double*)b[4].p, *dT1 = (double*)b[5].p, *dT2 = (double*)b[6].p, *dZa = (double*)b[7].p;
-  double *dZb = (double*)b[8].p, *dYb = (double*)b[9].p;
+  void *dY = b[0].p, *dZ = b[1].p, *P = b[2].p, *T = b[3].p, *dYa = b[4].p, *dT1 = b[5].p, *dT2 = b[6].p;
+  void *dZa = b[7].p, *dZb = b[8].p, *dYb = b[9].p;
+  const int64_t g = grid_of(nnz);
   // X = sqrt(c) Y_steps:  dY_steps = sqrt(c) dF,  dZ_steps = 0
-  if ((s = run_add(p, S_FP64, std::sqrt(c), dF, 0.0, nullptr, 0.0, dY, st))) return s;
-  SF_CUDA(cudaMemsetAsync(dZ, 0, sizeof(double) * nnz, st));
+  if (prec == S_FP32) {
+    convert_kernel<double, float><<<g, 256, 0, st>>>(nnz, dF, (float*)dY, std::sqrt(c));
+    SF_CUDA(cudaGetLastError());
+  } else if ((s = run_add(p, S_FP64, std::sqrt(c), dF, 0.0, nullptr, 0.0, dY, st))) {
+    return s;
+  }
+  SF_CUDA(cudaMemsetAsync(dZ, 0, w * nnz, st));
   for (int k = steps - 1; k >= 0; --k) {
-    const double* Y = ck + (int64_t)2 * k * nnz;
-    const double* Z = Y + nnz;
-    if ((s = run_mul(plan->fwd, S_FP64, Z, Y, P, st))) return s;                 // P = P_S(Z Y)
-    if ((s = run_add(p, S_FP64, -0.5, P, 0.0, nullptr, 1.5, T, st))) return s;   // T = (3I - P)/2
+    const void* Y = (const char*)ck + (int64_t)2 * k * nnz * (int64_t)w;
+    const void* Z = (const char*)Y + (int64_t)nnz * w;
+    if ((s = run_mul(plan->fwd, prec, Z, Y, P, st))) return s;                  // P = P_S(Z Y)
+    if ((s = run_add(p, prec, -0.5, P, 0.0, nullptr, 1.5, T, st))) return s;    // T = (3I - P)/2
     // Y' = P_S(Y T): dY_a = P_S(dY' T^T), dT_1 = P_S(Y^T dY')
     if ((s = s_mul_masked_adjoint(plan, dY, Y, T, dYa, dT1, st))) return s;
     // Z' = P_S(T Z): dT_2 = P_S(dZ' Z^T), dZ_a = P_S(T^T dZ')
     if ((s = s_mul_masked_adjoint(plan, dZ, T, Z, dT2, dZa, st))) return s;
     // T = (3I - P)/2: dP = -(dT_1 + dT_2)/2, kept in dT1
-    if ((s = run_add(p, S_FP64, -0.5, dT1, -0.5, dT2, 0.0, dT1, st))) return s;
+    if ((s = run_add(p, prec, -0.5, dT1, -0.5, dT2, 0.0, dT1, st))) return s;
     // P = P_S(Z Y): dZ_b = P_S(dP Y^T), dY_b = P_S(Z^T dP)
     if ((s = s_mul_masked_adjoint(plan, dT1, Z, Y, dZb, dYb, st))) return s;
-    if ((s = run_add(p, S_FP64, 1.0, dYa, 1.0, dYb, 0.0, dY, st))) return s;
-    if ((s = run_add(p, S_FP64, 1.0, dZa, 1.0, dZb, 0.0, dZ, st))) return s;
+    if ((s = run_add(p, prec, 1.0, dYa, 1.0, dYb, 0.0, dY, st))) return s;
+    if ((s = run_add(p, prec, 1.0, dZa, 1.0, dZb, 0.0, dZ, st))) return s;
   }
   // Y_0 = A / c
-  if ((s = run_add(p, S_FP64, 1.0 / c, dY, 0.0, nullptr, 0.0, dA, st))) return s;
+  if (prec == S_FP32) {
+    convert_kernel<float, double><<<g, 256, 0, st>>>(nnz, (const float*)dY, dA, 1.0 / c);
+    SF_CUDA(cudaGetLastError());
+  } else if ((s = run_add(p, S_FP64, 1.0 / c, dY, 0.0, nullptr, 0.0, dA, st))) {
+    return s;
+  }
   SF_CUDA(cudaStreamSynchronize(st));
-  return S_OK;
+  return s_plan_status(plan, st);
+}
+
+extern "C" s_status s_funm_sqrt_backward(s_pattern p, int steps, double c, const double* ck, const double* dF,
+                                         double* dA, void* stream) {
+  if (!p || !ck || !dF || !dA || steps < 1 || !(c > 0.0)) return set_error(S_ERR_ARG, "s_funm_sqrt_backward: bad argument");
+  if (!p->has_all_diag) return set_error(S_ERR_PATTERN, "s_funm_sqrt_backward: the pattern must hold every diagonal block");
+  return sqrt_backward(p, S_FP64, steps, c, ck, dF, dA, (cudaStream_t)stream);
+}
+
+extern "C" s_status s_funm_sqrt_backward_prec(s_pattern p, s_prec prec, int steps, double c, const void* ck,
+                                              const double* dF, double* dA, void* stream) {
+  if (!p || !ck || !dF || !dA || steps < 1 || !(c > 0.0))
+    return set_error(S_ERR_ARG, "s_funm_sqrt_backward_prec: bad argument");
+  if (prec != S_FP64 && prec != S_FP32) return set_error(S_ERR_ARG, "s_funm_sqrt_backward_prec: prec must be S_FP64 or S_FP32");
+  if (!p->has_all_diag)
+    return set_error(S_ERR_PATTERN, "s_funm_sqrt_backward_prec: the pattern must hold every diagonal block");
+  return sqrt_backward(p, prec, steps, c, ck, dF, dA, (cudaStream_t)stream);
 }
 
 extern "C" s_status s_quad_form(s_pattern p, const double* X, const double* z, double* out, void* stream) {

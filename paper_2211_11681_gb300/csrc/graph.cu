@@ -7,6 +7,7 @@
 struct s_graph_t {
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
+  s_plan plan = nullptr;  // for the time-out record of the captured product
 };
 
 using namespace sf;
@@ -36,12 +37,15 @@ extern "C" s_status s_graph_capture_mul(s_plan plan, const void* A, const void* 
     delete g;
     return st ? st : cuda_error(e, "s_graph_capture_mul");
   }
+  g->plan = plan;
   *out = g;
   return S_OK;
 }
 
 extern "C" s_status s_graph_launch(s_graph g, void* stream) {
   if (!g) return set_error(S_ERR_ARG, "s_graph_launch: NULL graph");
+  const s_status st = take_timeout(g->plan->fwd);
+  if (st) return st;
   SF_CUDA(cudaGraphLaunch(g->exec, (cudaStream_t)stream));
   return S_OK;
 }

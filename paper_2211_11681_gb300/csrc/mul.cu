@@ -1244,22 +1244,17 @@ static s_status build_panels(MulDesc* d, int edge, int P) {
 struct F32Variant {
   int tt, mr, mc, km;  // tile edge, lane micro-tile, largest lambda extent of one stage
   int panel;           // 0: one tile per warp; P > 0: row panels of up to P tiles per warp
+  int nt;              // K-major kernel with bulk-copy staging (mul_nt.cu), micro-tile per tile:
+                       // 1 = looped 4-wide steps, 2 = full 20-wide pieces unrolled
 };
-constexpr F32Variant kF32Variants[] = {{20, 4, 4, 20, 0}, {20, 4, 4, 40, 0}, {16, 4, 2, 32, 0},
-                                       {12, 3, 2, 36, 0}, {10, 2, 2, 40, 0}, {8, 2, 1, 32, 0},
-                                       {12, 3, 2, 12, 3}, {10, 2, 2, 10, 4}, {8, 2, 1, 8, 4}};
-constexpr int kNumF32Variants = 9;
+constexpr F32Variant kF32Variants[] = {{20, 0, 0, 20, 0, 1},  {20, 0, 0, 20, 0, 2},  {20, 4, 4, 20, 0, 0},
+                                       {20, 4, 4, 40, 0, 0},  {16, 4, 2, 32, 0, 0},  {12, 3, 2, 36, 0, 0},
+                                       {10, 2, 2, 40, 0, 0},  {8, 2, 1, 32, 0, 0},   {12, 3, 2, 12, 3, 0},
+                                       {10, 2, 2, 10, 4, 0},  {8, 2, 1, 8, 4, 0}};
+constexpr int kNumF32Variants = 11;
+constexpr int kF32Fallback = 2;  // tile kernel of the K-major variants' tile list, for unaligned buffers
 
-static int g_sms = 0;
-static int num_sms() {
-  if (!g_sms) {
-    int dev = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&g_sms, cudaDevAttrMultiProcessorCount, dev);
-    if (g_sms <= 0) g_sms = 1;
-  }
-  return g_sms;
-}
+static int num_sms() { return sm_count(); }
 
 static Side side_of(const s_pattern_t* p, bool row_side, bool trans) {
   // row_side: the list indexed by the output row (X side); otherwise by the output column.
@@ -1348,6 +1343,15 @@ s_status build_desc(const s_pattern_t* X, bool tx, const s_pattern_t* Y, bool ty
   }
   cudaFree(dtrip);
   cudaFree(bflops);
+  if (e == cudaSuccess) {
+    // the time-out word lives in pinned host memory mapped into the device: a kernel's store
+    // reaches the host without a copy, and the next call on the plan reads it without a sync
+    e = cudaHostAlloc((void**)&d.err_host, sizeof(unsigned int), cudaHostAllocMapped);
+    if (e == cudaSuccess) {
+      *(volatile unsigned int*)d.err_host = 0u;
+      e = cudaHostGetDevicePointer((void**)&d.err, d.err_host, 0);
+    }
+  }
   if (e != cudaSuccess) st = cuda_error(e, "s_plan_create(symbolic)");
   if (!st) st = build_tiles(&d, kF32Variants[0].tt);
   if (!st && prec == S_BF16X3) {
@@ -1362,6 +1366,7 @@ s_status build_desc(const s_pattern_t* X, bool tx, const s_pattern_t* Y, bool ty
     }
   }
   if (!st && prec == S_TF32X3) st = tc_prepare(&d);
+  if (!st && prec == S_FP32) st = nt_configure(&d, tx, ty, false);
   if (!st && prec == S_FP64_DF) {
     // split operands (float pairs), reused by every call of this plan
     e = cudaMalloc(&d.df_x, sizeof(float2) * std::max<int64_t>(X->d.nnz, 1));
@@ -1378,8 +1383,11 @@ s_status build_desc(const s_pattern_t* X, bool tx, const s_pattern_t* Y, bool ty
 
 void free_desc(MulDesc* d) {
   tc_free(d);
-  cudaFree(d->tc_err);
-  d->tc_err = nullptr;
+  nt_free_side(&d->ntx);
+  nt_free_side(&d->nty);
+  if (d->err_host) cudaFreeHost(d->err_host);
+  d->err_host = nullptr;
+  d->err = nullptr;
   cudaFree(d->ptiles);
   cudaFree(d->pidx);
   d->ptiles = nullptr;
@@ -1402,6 +1410,7 @@ using F32Kernel = void (*)(MulArgs, const float*, const float*, float*);
 
 template <int V>
 static F32Kernel f32_kernel(bool tx, bool ty) {
+  static_assert(kF32Variants[V].nt == 0 && kF32Variants[V].panel == 0, "tile variant expected");
   constexpr int TT = kF32Variants[V].tt, MR = kF32Variants[V].mr, MC = kF32Variants[V].mc, KM = kF32Variants[V].km;
   return tx ? (ty ? mul_f32_kernel<TT, MR, MC, KM, true, true> : mul_f32_kernel<TT, MR, MC, KM, true, false>)
             : (ty ? mul_f32_kernel<TT, MR, MC, KM, false, true> : mul_f32_kernel<TT, MR, MC, KM, false, false>);
@@ -1419,12 +1428,12 @@ static F32PanelKernel f32_panel_kernel(bool tx, bool ty) {
 
 static F32Kernel f32_kernel_of(int v, bool tx, bool ty) {
   switch (v) {
-    case 1: return f32_kernel<1>(tx, ty);
-    case 2: return f32_kernel<2>(tx, ty);
     case 3: return f32_kernel<3>(tx, ty);
     case 4: return f32_kernel<4>(tx, ty);
     case 5: return f32_kernel<5>(tx, ty);
-    default: return f32_kernel<0>(tx, ty);
+    case 6: return f32_kernel<6>(tx, ty);
+    case 7: return f32_kernel<7>(tx, ty);
+    default: return f32_kernel<2>(tx, ty);
   }
 }
 
@@ -1450,9 +1459,9 @@ static s_status launch_f32_panel(const MulDesc& d, const void* X, const void* Y,
   a.ntiles = d.ntiles;
   a.counter = d.counter;
   SF_CUDA(cudaMemsetAsync(d.counter, 0, sizeof(unsigned int), st));
-  F32PanelKernel kern = d.variant == 6   ? f32_panel_kernel<6>(d.x.trans, d.y.trans)
-                        : d.variant == 7 ? f32_panel_kernel<7>(d.x.trans, d.y.trans)
-                                         : f32_panel_kernel<8>(d.x.trans, d.y.trans);
+  F32PanelKernel kern = d.variant == 8   ? f32_panel_kernel<8>(d.x.trans, d.y.trans)
+                        : d.variant == 9 ? f32_panel_kernel<9>(d.x.trans, d.y.trans)
+                                         : f32_panel_kernel<10>(d.x.trans, d.y.trans);
   const size_t smem = f32_smem(d.variant);
   SF_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   int per_sm = 0;
@@ -1488,9 +1497,14 @@ static s_status launch_typed(const MulDesc& d, const void* X, const void* Y, voi
   if constexpr (sizeof(T) == 4) {
     if (kF32Variants[d.variant].panel) return launch_f32_panel(d, X, Y, C, st);
     if (d.edge != kF32Variants[d.variant].tt) return set_error(S_ERR_ARG, "internal: tile list does not match variant");
-    kern = f32_kernel_of(d.variant, d.x.trans, d.y.trans);
+    int v = d.variant;
+    if (kF32Variants[v].nt) {
+      if (nt_usable(d, X, Y)) return launch_nt(d, X, Y, C, st, kF32Variants[v].nt == 2);
+      v = kF32Fallback;  // same tile list (edge 20); reads any alignment
+    }
+    kern = f32_kernel_of(v, d.x.trans, d.y.trans);
     warps = kF32Warps;
-    dsmem = f32_smem(d.variant);
+    dsmem = f32_smem(v);
     SF_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dsmem));
   } else {
     if (d.edge != kTile) return set_error(S_ERR_ARG, "internal: double kernel needs 20-wide tiles");
@@ -1591,6 +1605,15 @@ static s_status launch_bf16x3(const MulDesc& d, const void* X, const void* Y, vo
   return S_OK;
 }
 
+s_status take_timeout(const MulDesc& d) {
+  volatile unsigned int* w = d.err_host;
+  if (!w || *w == 0u) return S_OK;
+  *w = 0u;
+  return set_error(S_ERR_TIMEOUT,
+                   "an earlier product of this plan gave up waiting on its own device-side copies or tensor-core "
+                   "work; its outputs are unspecified (NaN where written after the time-out)");
+}
+
 s_status run_mul(const MulDesc& d, s_prec prec, const void* X, const void* Y, void* C, cudaStream_t st) {
   switch (prec) {
     case S_FP64:
@@ -1648,6 +1671,23 @@ extern "C" s_status s_plan_destroy(s_plan p) {
     free_desc(&p->adjB);
   }
   delete p;
+  return S_OK;
+}
+
+extern "C" s_status s_plan_status(s_plan p, void* stream) {
+  if (!p) return set_error(S_ERR_ARG, "s_plan_status: NULL plan");
+  SF_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
+  s_status st = take_timeout(p->fwd);
+  if (p->adj_built) {
+    const s_status sa = take_timeout(p->adjA), sb = take_timeout(p->adjB);
+    if (!st) st = sa ? sa : sb;
+  }
+  return st;
+}
+
+extern "C" s_status s_plan_timeout_word(s_plan p, unsigned int** word) {
+  if (!p || !word) return set_error(S_ERR_ARG, "s_plan_timeout_word: NULL argument");
+  *word = p->fwd.err_host;
   return S_OK;
 }
 
@@ -1765,7 +1805,7 @@ extern "C" s_status s_plan_variant(s_plan p, int variant, int* tile, int* micro_
     return S_OK;
   }
   if (variant >= kNumF32Variants) return set_error(S_ERR_ARG, "s_plan_variant: no such variant");
-  if (tile) *tile = kF32Variants[variant].tt;
+  if (tile) *tile = kF32Variants[variant].tt;  // K-major variant: micro-tile 0 x 0 = per tile
   if (micro_rows) *micro_rows = kF32Variants[variant].mr;
   if (micro_cols) *micro_cols = kF32Variants[variant].mc;
   if (stage_k) *stage_k = kF32Variants[variant].km;
@@ -1824,5 +1864,7 @@ extern "C" s_status s_plan_set_symmetric_a(s_plan p, int symmetric) {
   // read A(nu, lambda) as the transpose of the stored block (lambda, nu): same values when A
   // is symmetric, and column-contiguous staging for the float kernel
   p->fwd.x = side_of(A, true, symmetric != 0);
+  // the K-major float kernel reads A as stored and, for B = A, B(lambda, nu') through A's rows
+  if (p->prec == S_FP32) return nt_configure(&p->fwd, false, false, symmetric != 0 && p->b == p->a);
   return S_OK;
 }

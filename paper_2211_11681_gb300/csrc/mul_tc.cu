@@ -52,16 +52,7 @@ static_assert(kTcS * kTcN <= kTcCols, "tensor memory");
 static_assert(kTcKC % 8 == 0 && kTcSmem <= 200 * 1024 && kTcD < kTcS, "stage buffers");
 static_assert(sizeof(TcEntry) % 16 == 0, "entries move as 16-byte words");
 
-int g_tc_sms = 0;
-int tc_num_sms() {
-  if (!g_tc_sms) {
-    int dev = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&g_tc_sms, cudaDevAttrMultiProcessorCount, dev);
-    if (g_tc_sms <= 0) g_tc_sms = 1;
-  }
-  return g_tc_sms;
-}
+int tc_num_sms() { return sm_count(); }
 
 __device__ __forceinline__ uint32_t tc_smem(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -261,7 +252,8 @@ __device__ __forceinline__ void tc_wait(uint64_t* bar, uint32_t parity, volatile
     if (done) return;
     if (clock64() - t0 > (1ll << 31)) {
       *abort = 1;
-      atomicExch(err, 1u);
+      *(volatile unsigned int*)err = 1u;  // host-mapped word: a plain store, then a system fence
+      __threadfence_system();
       return;
     }
     if (*abort) return;
@@ -601,16 +593,14 @@ s_status tc_prepare(MulDesc* d) {
   if (e == cudaSuccess) e = cudaMalloc(&d->tc_xl, sizeof(float) * nx);
   if (e == cudaSuccess && own_y) e = cudaMalloc(&d->tc_yh, sizeof(float) * ny);
   if (e == cudaSuccess && own_y) e = cudaMalloc(&d->tc_yl, sizeof(float) * ny);
-  if (e == cudaSuccess && !d->tc_err) {
-    e = cudaMalloc(&d->tc_err, sizeof(unsigned int));
-    if (e == cudaSuccess) e = cudaMemset(d->tc_err, 0, sizeof(unsigned int));
-  }
   if (e != cudaSuccess) return cuda_error(e, "S_TF32X3 plan");
   return S_OK;
 }
 
 s_status launch_tc(const MulDesc& d, const void* X, const void* Y, void* C, cudaStream_t st) {
   if (!d.tc_pstart || !d.tc_xh || !d.tc_xl) return set_error(S_ERR_ARG, "internal: S_TF32X3 plan not prepared");
+  s_status s0 = take_timeout(d);
+  if (s0) return s0;
   if (d.tc_sym && X != Y)
     return set_error(S_ERR_ARG, "s_mul_masked: a symmetric S_TF32X3 plan must be called with B = A");
   s_status s;
@@ -645,7 +635,7 @@ s_status launch_tc(const MulDesc& d, const void* X, const void* Y, void* C, cuda
   a.yl = yl;
   a.C = (float*)C;
   a.counter = d.counter;
-  a.err = d.tc_err;
+  a.err = d.err;
   SF_CUDA(cudaFuncSetAttribute(mul_tf32x3_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTcSmem));
   const int grid = (int)std::min<int64_t>(d.npanels, (int64_t)tc_num_sms());
   mul_tf32x3_kernel<<<grid, kTcThreads, kTcSmem, st>>>(a);

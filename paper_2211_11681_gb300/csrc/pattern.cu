@@ -1,6 +1,7 @@
 // Block patterns: validation, host/device copies, block-CSC index, tree hash.
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <new>
 
 #include "common.cuh"
@@ -17,6 +18,22 @@ s_status set_error(s_status st, const std::string& msg) {
 s_status cuda_error(cudaError_t e, const char* what) {
   return set_error(e == cudaErrorMemoryAllocation ? S_ERR_NOMEM : S_ERR_CUDA,
                    std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+// SM count of the current device, queried once per device ordinal (grids are sized from it,
+// so a plan made on one device must not inherit another device's count).
+int sm_count() {
+  static std::mutex mu;
+  static int cache[256] = {};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 256) return 1;
+  std::lock_guard<std::mutex> lk(mu);
+  if (cache[dev] <= 0) {
+    int n = 0;
+    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) n = 1;
+    cache[dev] = n;
+  }
+  return cache[dev];
 }
 
 template <typename T>

@@ -43,6 +43,8 @@ def _load():
         "s_plan_create": (i32, [vp, vp, vp, i32, P(vp)]),
         "s_plan_destroy": (i32, [vp]),
         "s_plan_stats": (i32, [vp, P(i64), P(dbl)]),
+        "s_plan_status": (i32, [vp, vp]),
+        "s_plan_timeout_word": (i32, [vp, P(P(ctypes.c_uint))]),
         "s_plan_autotune": (i32, [vp, vp, vp, vp, vp, P(i32)]),
         "s_plan_variant": (i32, [vp, i32, P(i32), P(i32), P(i32), P(i32)]),
         "s_plan_set_variant": (i32, [vp, i32]),
@@ -57,9 +59,11 @@ def _load():
         "s_mul_masked_adjoint": (i32, [vp, vp, vp, vp, vp, vp, vp]),
         "s_add": (i32, [vp, i32, dbl, vp, dbl, vp, dbl, vp, vp]),
         "s_norm_est": (i32, [vp, vp, i32, P(dbl), vp]),
+        "s_spmm": (i32, [vp, vp, vp, i32, vp, vp]),
         "s_norm_est_noalloc": (i32, [vp, vp, i32, P(dbl), vp]),
         "s_funm": (i32, [vp, i32, vp, vp, vp, vp]),
         "s_funm_sqrt_backward": (i32, [vp, i32, dbl, vp, vp, vp, vp]),
+        "s_funm_sqrt_backward_prec": (i32, [vp, i32, i32, dbl, vp, vp, vp, vp]),
         "s_quad_form": (i32, [vp, vp, vp, P(dbl), vp]),
         "s_quad_form_grad": (i32, [vp, vp, vp, vp]),
         "s_last_error": (ctypes.c_char_p, []),
@@ -118,6 +122,14 @@ def pattern_arrays(h):
     return np.ctypeslib.as_array(bo, shape=(n + 1,)).copy(), rowptr, colidx
 
 
+def pattern_dim(h):
+    """Matrix dimension of a pattern handle (its last block offset)."""
+    nc = ctypes.c_int32()
+    bo, rp, ci = ctypes.POINTER(ctypes.c_int64)(), ctypes.POINTER(ctypes.c_int64)(), ctypes.POINTER(ctypes.c_int32)()
+    check(lib.s_pattern_host_arrays(h, ctypes.byref(nc), ctypes.byref(bo), ctypes.byref(rp), ctypes.byref(ci)))
+    return int(bo[nc.value])
+
+
 class Pattern:
     """A block pattern S on the device (s_pattern_create)."""
 
@@ -141,6 +153,11 @@ class Pattern:
     @property
     def nblocks(self):
         return int(lib.s_pattern_nblocks(self.h))
+
+    @property
+    def n(self):
+        """Matrix dimension (the last block offset)."""
+        return pattern_dim(self.h)
 
     def block_offsets(self):
         out = np.zeros(self.nblocks + 1, dtype=np.int64)
@@ -208,6 +225,17 @@ class Plan:
     def mul(self, A, B, C, stream=None):
         check(lib.s_mul_masked(self.h, _ptr(A), _ptr(B), _ptr(C), _stream(stream)))
         return C
+
+    def status(self, stream=None):
+        """Synchronise the stream and raise SFormatError(S_ERR_TIMEOUT) if a bounded device
+        wait of an earlier product of this plan ran out (s_plan_status)."""
+        check(lib.s_plan_status(self.h, _stream(stream)))
+
+    def timeout_word(self):
+        """ctypes pointer to the plan's host-mapped time-out word (None when it has none)."""
+        w = ctypes.POINTER(ctypes.c_uint)()
+        check(lib.s_plan_timeout_word(self.h, ctypes.byref(w)))
+        return w if w else None
 
     def adjoint(self, dC, A, B, dA=None, dB=None, stream=None):
         check(lib.s_mul_masked_adjoint(self.h, _ptr(dC), _ptr(A), _ptr(B), _ptr(dA), _ptr(dB), _stream(stream)))
@@ -278,6 +306,15 @@ def add(pattern, A, B, C, alpha=1.0, beta=1.0, gamma=0.0, prec="fp64", stream=No
     return C
 
 
+def spmm(pattern, A, X, Y, stream=None):
+    """Y = A X for a double value buffer A and N x k matrices X, Y stored column-major (torch
+    tensors of shape (k, N), contiguous, float64) (s_spmm)."""
+    if X.dim() != 2 or Y.shape != X.shape or X.shape[1] != pattern.n:
+        raise ValueError("spmm: X and Y must have shape (k, N)")
+    check(lib.s_spmm(pattern.h, _ptr(A), _ptr(X), int(X.shape[0]), _ptr(Y), _stream(stream)))
+    return Y
+
+
 def norm_est(pattern, A, iters=50, stream=None):
     lam = ctypes.c_double()
     check(lib.s_norm_est(pattern.h, _ptr(A), int(iters), ctypes.byref(lam), _stream(stream)))
@@ -307,9 +344,11 @@ def version():
     return lib.s_version().decode()
 
 
-def sqrt_backward(pattern, steps, c, checkpoints, dF, dA, stream=None):
-    check(lib.s_funm_sqrt_backward(pattern.h, int(steps), float(c), _ptr(checkpoints), _ptr(dF), _ptr(dA),
-                                   _stream(stream)))
+def sqrt_backward(pattern, steps, c, checkpoints, dF, dA, prec="fp64", stream=None):
+    """dA of the Newton-Schulz square root from its checkpoints (double for "fp64", float for
+    "fp32")."""
+    check(lib.s_funm_sqrt_backward_prec(pattern.h, PREC[prec], int(steps), float(c), _ptr(checkpoints), _ptr(dF),
+                                        _ptr(dA), _stream(stream)))
     return dA
 
 

@@ -49,5 +49,18 @@ def test_builder_threshold_is_symmetric_and_close_to_oracle():
     pat, vals = b.values(w.nu, w.ell, 1.0 / n, w.nugget, w.tau)
     off = pat.block_offsets()
     assert off[-1] == pat.nnz
-    # kept blocks agree with the oracle's FP64 decision up to a few borderline blocks
-    assert abs(pat.nblocks - c.A.nblocks) <= max(3, c.A.nblocks // 1000)
+    # kept blocks: the device decides on float values (within 2e-6 of the largest entry of
+    # the FP64 ones, test above), so only pairs whose largest magnitude lies within that
+    # band around tau may be decided differently; every other block is kept by both or by
+    # neither
+    bo, rp, ci = pat.arrays()
+    got = {(i, int(ci[k])) for i in range(len(rp) - 1) for k in range(rp[i], rp[i + 1])}
+    want = {(int(c.A.brow[k]), int(c.A.colidx[k])) for k in range(c.A.nblocks)}
+    assert got == {(j, i) for (i, j) in got}
+    K = np.abs(c.Khat)
+    K = np.maximum(K, K.T)
+    band = 2e-6 * np.abs(c.A.val).max()
+    boff = c.A.boff
+    for (i, j) in got ^ want:
+        m = K[boff[i]:boff[i + 1], boff[j]:boff[j + 1]].max()
+        assert i != j and abs(m - w.tau) <= band, (i, j, m)

@@ -1,7 +1,7 @@
 """Parity at the benchmark's full size (N = 2^20 points in [0,1]^3, Matern-1/2, ell = 0.1,
-q = 3, leaf 32, eta = 1.0, tau = 1e-8), in the launch configuration bench.py times: the
-FP64, mixed (compensated float), split-bfloat16 and split-TF32 tensor-core products of the whole
-pattern on the GPU, compared on a seeded sample of
+q = 3, leaf 32, eta = 1.0, tau = 1e-8), in the launch configuration bench.py times (symmetric A, float
+kernel shape picked by the autotuner on this pattern): the FP64, mixed (compensated float),
+split-bfloat16 and split-TF32 tensor-core products of the whole pattern on the GPU, compared on a seeded sample of
 output blocks that the FP64 oracle computes one by one (plus every block of the root's row,
 whose lambda lists are the longest, and the last block).
 
@@ -34,9 +34,14 @@ def c2():
     sf.Plan(pat, pat, pat, "fp64").mul(vals, vals, C64)
     A32 = vals.float()
     C32 = torch.empty_like(A32)
+    # the timed configuration of bench.py: symmetric A, kernel shape chosen by the autotuner
     p32 = sf.Plan(pat, pat, pat, "fp32")
-    p32.set_symmetric_a(True)          # as bench.py: A = T K T^T is symmetric
+    p32.set_symmetric_a(True)
+    shape = p32.autotune(A32, A32, C32)
+    C32.fill_(float("nan"))
     p32.mul(A32, A32, C32)
+    assert p32.variant() == shape
+    print("fullsize: autotuned float variant %d %s" % (p32.variant_index, shape))
     Cb = torch.empty_like(A32)
     pb = sf.Plan(pat, pat, pat, "bf16x3")
     pb.set_symmetric_a(True)

@@ -94,3 +94,21 @@ def test_empty_output_and_empty_operands():
     A = random_bcsr(bsize, 1.0, 3)
     assert product.mul_masked(A, A, Z).val.size == 0
     np.testing.assert_array_equal(product.mul_masked(Z, A, A).val, 0.0)
+
+
+def test_product_of_two_kernels_on_three_eta_patterns():
+    # K_A and K_B compressed on one tree with different kernels and different eta, C on a
+    # third eta pattern: the oracle product equals the dense product masked to S_C
+    from oracle.pattern import eta_pattern
+    S = W.PAIR_2D
+    w = W.Workload("pair", S["seed"], 500, S["d"], "cube", 0.0, 0.0, 0.0, S["q"], S["leaf"], 0.0, 0.0)
+    x = W.points(w)
+    (nua, la, ea), (nub, lb, eb) = S["a"], S["b"]
+    ca = compress_kernel(x, nua, la, S["q"], S["leaf"], ea, 0.0, 1.0 / 500, S["nugget"])
+    cb = compress_kernel(x, nub, lb, S["q"], S["leaf"], eb, 0.0, 1.0 / 500, S["nugget"])
+    rp, ci = eta_pattern(ca.clusters, ca.basis.bsize, S["c_eta"])
+    Cp = BlockCSR(ca.A.bsize, rp, ci)
+    C = product.mul_masked(ca.A, cb.A, Cp)
+    want = (ca.A.to_dense() @ cb.A.to_dense()) * Cp.mask()
+    np.testing.assert_allclose(C.to_dense(), want, atol=1e-13 * np.abs(want).max())
+    assert Cp.nblocks < cb.A.nblocks < ca.A.nblocks

@@ -35,11 +35,24 @@ def test_noalloc_norm_estimate_matches_allocating_one():
         st = sf.lib.s_norm_est_noalloc(P.h, ctypes.c_void_p(A.data_ptr()), 50, ctypes.byref(lam), stream)
         assert st == sf.S_OK, sf.lib.s_last_error().decode()
         assert lam.value == pytest.approx(want, rel=1e-12)
-    # a second, different matrix on a smaller pattern after the first: no stale state
+    # a different matrix on the same pattern
     B = dev(c.A.val * 3.0)
     lam = ctypes.c_double(-1.0)
     assert sf.lib.s_norm_est_noalloc(P.h, ctypes.c_void_p(B.data_ptr()), 50, ctypes.byref(lam), stream) == sf.S_OK
     assert lam.value == pytest.approx(3.0 * want, rel=1e-12)
+    # then a smaller matrix (N = 1024) on its own, smaller pattern: the array still holds the
+    # larger call's vectors beyond N = 1024, which must not leak into this one
+    m = 1024
+    xs = W.points(w, m, seed=77)
+    cs = compress_kernel(xs, w.nu, w.ell, w.q, w.leaf, w.eta, w.tau, 1.0 / m, w.nugget)
+    Ps = sf.Pattern(cs.A.boff, np.array([cl.level for cl in cs.clusters], dtype=np.int32), cs.A.rowptr,
+                    cs.A.colidx)
+    As = dev(cs.A.val)
+    want_s = sf.norm_est(Ps, As, 50)
+    lam = ctypes.c_double(-1.0)
+    st = sf.lib.s_norm_est_noalloc(Ps.h, ctypes.c_void_p(As.data_ptr()), 50, ctypes.byref(lam), stream)
+    assert st == sf.S_OK, sf.lib.s_last_error().decode()
+    assert lam.value == pytest.approx(want_s, rel=1e-12)
 
 
 def test_noalloc_rejects_oversized_pattern():

@@ -16,6 +16,16 @@ Sec. 5.3):
                       Matern-3/2, ell ~ U[0.05, 0.5], q=2, leaf 16, eta=1.25.
   matern32_3d_grad    N=2^20 uniform [0,1]^3, Matern-3/2, ell=0.15, q=2, 10 NS steps,
                       gradient checked at N=4096.
+  paper_mult_2d/3d    the multiplication benchmark of Sec. 5.1: uniform [0,1]^d, the
+                      exponential kernel exp(-r)/N (Matern-1/2, ell=1), q+1 = 4 vanishing
+                      moments (q=3), eta=1.25, a-posteriori tau = 1e-5/N, leaf 2*m_q (20 in
+                      2D, 40 in 3D); N from 5,000 to 1,000,000 (PAPER_MULT_NS).  The second
+                      factor is the first with every stored entry a scaled by (1 + 0.1 u),
+                      u uniform in [0,1] (perturbation_factors).
+  pair_2d_4096        two kernels on one tree for a product of different matrices: N=4096
+                      uniform [0,1]^2, q=2, leaf 16; A Matern-3/2 ell=0.2 on the eta=1.25
+                      pattern, B Matern-5/2 ell=0.1 on the eta=1.0 pattern, C on the eta=0.8
+                      pattern (PAIR_2D).
 """
 from dataclasses import dataclass, replace
 
@@ -53,6 +63,39 @@ WORKLOADS = {
     "matern32_2d_batch": Workload("matern32_2d_batch", 4, 0, 2, "cube", 1.5, 0.0, 0.0, 2, 16, 1.25, 0.0),
     "matern32_3d_grad": Workload("matern32_3d_grad", 5, 1 << 20, 3, "cube", 1.5, 0.15, 0.0, 2, 16, 1.25, 0.0),
 }
+
+
+PAPER_MULT_NS = (5000, 10000, 50000, 100000, 250000, 500000, 1000000)
+
+PAPER_MULT = {
+    "paper_mult_2d": Workload("paper_mult_2d", 6, 100000, 2, "cube", 0.5, 1.0, 0.0, 3, 20, 1.25, 1e-5),
+    "paper_mult_3d": Workload("paper_mult_3d", 7, 100000, 3, "cube", 0.5, 1.0, 0.0, 3, 40, 1.25, 1e-5),
+}
+WORKLOADS.update(PAPER_MULT)
+
+# Product of two different kernels on one tree (same points, leaf and q), three patterns:
+# (nu, ell, eta) of A, of B, and the eta of C's pattern.
+PAIR_2D = {"seed": 8, "n": 4096, "d": 2, "q": 2, "leaf": 16,
+           "a": (1.5, 0.2, 1.25), "b": (2.5, 0.1, 1.0), "c_eta": 0.8, "nugget": 1e-3}
+
+
+def tau_of(w, n):
+    """Absolute threshold of a workload at size n: the paper-benchmark workloads state tau
+    relative to 1/N (tau = 1e-5/N), the others absolutely."""
+    return w.tau / n if w.name.startswith("paper_mult") else w.tau
+
+
+def perturbation_factors(count, seed):
+    """1 + 0.1 u with u uniform in [0, 1): the factors of the perturbed second operand of the
+    multiplication benchmark, one per stored entry (host, FP64)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    return 1.0 + 0.1 * rng.random(count)
+
+
+def estimator_probe(n, k=10, seed=99):
+    """The N x k matrix X of independent uniform [0,1) entries of the e_F estimator."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    return rng.random((n, k))
 
 
 def points(w, n=None, seed=None):
