@@ -50,6 +50,8 @@ def parse():
     ap.add_argument("--batch", type=int, default=256, help="matrices of the batched workload")
     ap.add_argument("--precisions", default="fp64,fp64_df,mixed", help="drivers mode: arithmetic forms to run")
     ap.add_argument("--tau", type=float, default=None, help="override the workload's threshold")
+    ap.add_argument("--variant", type=int, default=-1,
+                    help="float kernel variant to time (default: the autotuner's choice)")
     ap.add_argument("--sizes", default="5000,10000,50000,100000,250000,500000,1000000",
                     help="paper_mult_2d/3d: the N of the sweep")
     ap.add_argument("--product", choices=["fp32", "tf32x3", "bf16x3"], default="fp32",
@@ -236,27 +238,42 @@ def run_reference(args, w, n, rank, world):
 def run_batch(args, rank, world):
     """256 independent matrices, N log-uniform in [2^10, 2^16], concatenated into one pattern:
     one graph-replayed persistent launch per batched step, against a loop of one launch per
-    matrix (same kernel variant).  Metric: masked products per second."""
+    matrix (same kernel variant).  Metric: masked products per second.  The values of each
+    matrix are built on the device and kept in float only, in slices of one buffer."""
     import torch
     import workloads as W
     from paper_2211_11681_gb300 import sformat as sf
     from paper_2211_11681_gb300.builder import Builder
     ws = W.batch_workloads(count=args.batch)
     t0 = time.time()
-    pats, vals = [], []
+    pats, parts = [], []
+    t_host = t_dev = 0.0
     for w in ws:
+        ta = time.time()
         b = Builder(W.points(w), w.leaf, w.q, w.eta)
+        tb = time.time()
         p, v = b.values(w.nu, w.ell, 1.0 / w.n, w.nugget, 0.0)
         pats.append(p)
-        vals.append(v.float())
-        del b
-    prep = time.time() - t0
+        parts.append(v.float())
+        del b, v
+        t_host += tb - ta
+        t_dev += time.time() - tb
     P = sf.concat(pats)
-    A = torch.cat(vals)
+    A = torch.empty(max(P.nnz, 1), dtype=torch.float32, device="cuda")
+    offs = [0]
+    for v in parts:
+        A[offs[-1]:offs[-1] + v.numel()].copy_(v)
+        offs.append(offs[-1] + v.numel())
+    del parts
+    torch.cuda.empty_cache()
+    prep = time.time() - t0
     C = torch.empty_like(A)
     plan = sf.Plan(P, P, P, "fp32")
+    plan.set_symmetric_a(True)                 # every part is a symmetric kernel matrix
     triples, flops = plan.stats()
+    t1 = time.time()
     shape = plan.autotune(A, A, C)
+    tune_s = time.time() - t1
     g = plan.graph(A, A, C)
     stream = torch.cuda.current_stream()
     for _ in range(args.warmup):
@@ -276,22 +293,25 @@ def run_batch(args, rank, world):
         e1.record(stream)
         torch.cuda.synchronize()
     ms = e0.elapsed_time(e1) / args.steps
-    # one launch per matrix, same variant
-    plans, outs = [], []
+    variant = plan.variant_index
+    del g, plan
+    torch.cuda.empty_cache()
+    # one launch per matrix, same variant, on slices of the same buffers
+    plans = []
     for p in pats:
         q = sf.Plan(p, p, p, "fp32")
-        q.set_variant(plan.variant_index)
+        q.set_symmetric_a(True)
+        q.set_variant(variant)
         plans.append(q)
-    for v in vals:
-        outs.append(torch.empty_like(v))
+    views = [(A[offs[i]:offs[i + 1]], C[offs[i]:offs[i + 1]]) for i in range(len(pats))]
     for _ in range(args.warmup):
-        for q, v, o in zip(plans, vals, outs):
-            q.mul(v, v, o)
+        for q, (a, c) in zip(plans, views):
+            q.mul(a, a, c)
     torch.cuda.synchronize()
     e0.record(stream)
     for _ in range(args.steps):
-        for q, v, o in zip(plans, vals, outs):
-            q.mul(v, v, o)
+        for q, (a, c) in zip(plans, views):
+            q.mul(a, a, c)
     e1.record(stream)
     torch.cuda.synchronize()
     ms_loop = e0.elapsed_time(e1) / args.steps
@@ -303,9 +323,10 @@ def run_batch(args, rank, world):
             "config": {"workload": "matern32_2d_batch", "matrices": n, "n_total": int(sum(w.n for w in ws)),
                        "n_min": int(min(w.n for w in ws)), "n_max": int(max(w.n for w in ws)),
                        "nnz": P.nnz, "blocks": P.nblocks, "triples": triples, "flops_per_step": flops,
-                       "prep_seconds": round(prep, 1), "l2": "inputs larger than L2, no flush"},
-            "gflops": flops / (ms * 1e-3) / 1e9, "autotuned_variant": shape,
-            "tune_ms": None,
+                       "prep_seconds": round(prep, 1), "host_builder_s": round(t_host, 1),
+                       "device_values_s": round(t_dev, 1), "autotune_s": round(tune_s, 1),
+                       "l2": "inputs larger than L2, no flush"},
+            "gflops": flops / (ms * 1e-3) / 1e9, "autotuned_variant": shape, "variant_index": variant,
             "loop": {"ms_per_step": round(ms_loop, 3), "products_per_s": n / (ms_loop * 1e-3),
                      "launches_per_step": n},
             "batched_speedup_vs_loop": ms_loop / ms, "clocks": clk.summary(), "gpu_launches": args.steps}
@@ -568,7 +589,11 @@ def main():
     C32 = torch.empty_like(A32)
     stream = torch.cuda.current_stream()
     t0 = time.time()
-    shape = plan32.autotune(A32, A32, C32)      # kernel shape for this pattern
+    if args.variant >= 0 and args.product == "fp32":
+        plan32.set_variant(args.variant)         # fixed shape (profiling runs)
+        shape = plan32.variant()
+    else:
+        shape = plan32.autotune(A32, A32, C32)  # kernel shape for this pattern
     prep["autotune_s"] = round(time.time() - t0, 2)
     for _ in range(args.warmup):
         plan32.mul(A32, A32, C32)

@@ -143,9 +143,10 @@ int s_plan_num_variants_of(s_plan plan);
 s_status s_plan_set_symmetric_a(s_plan plan, int symmetric);
 /* Shape of a variant of the plan's arithmetic (variant < 0: the current one): output tile edge, the
  * micro-tile of one lane, and the largest lambda extent staged at once (consecutive small
- * lambda blocks are packed into one stage up to this extent).  Float variant 0 (the default)
- * is the K-major kernel: each lambda block staged by one bulk copy, the micro-tile a quarter
- * of each tile's padded edge (reported as 0 x 0), lambda staged in pieces of at most 20.  For an S_TF32X3 plan: 32 rows
+ * lambda blocks are packed into one stage up to this extent).  Float variants 0 (the default)
+ * and 1 are the K-major kernel: each lambda block staged by one bulk copy, the micro-tile a
+ * quarter of each tile's padded edge (reported as 0 x 0), lambda staged in pieces of at most
+ * 20; variant 1 addresses full 20-wide pieces with a compile-time row pitch.  For an S_TF32X3 plan: 32 rows
  * of a panel, 128 MMA rows (member columns), 32 MMA columns, lambda extent 24 per stage.
  * Any output may be NULL. */
 s_status s_plan_variant(s_plan plan, int variant, int* tile, int* micro_rows, int* micro_cols, int* stage_k);

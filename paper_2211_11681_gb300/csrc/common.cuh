@@ -102,6 +102,7 @@ struct NtSideDesc {
   const s_pattern_t* pat = nullptr;
   bool prep = false;              // true: the kernel reads `scratch`
   bool trans = false;             // prepared copy holds the stored blocks transposed
+  bool from_x = false;            // Y side: reads the X side's prepared copy (B = A, symmetric)
   int64_t* poff = nullptr;
   float* scratch = nullptr;
   int64_t len = 0;
@@ -154,7 +155,7 @@ s_status take_timeout(const MulDesc& d);
 // with these buffers can use it, the launch, and the release of its scratch.
 s_status nt_configure(MulDesc* d, bool x_trans, bool y_trans, bool y_sym);
 bool nt_usable(const MulDesc& d, const void* X, const void* Y);
-s_status launch_nt(const MulDesc& d, const void* X, const void* Y, void* C, cudaStream_t st, bool unroll);
+s_status launch_nt(const MulDesc& d, const void* X, const void* Y, void* C, cudaStream_t st, bool const_pitch);
 void nt_free_side(NtSideDesc* s);
 s_status run_mul(const MulDesc& d, s_prec prec, const void* X, const void* Y, void* C, cudaStream_t st);
 

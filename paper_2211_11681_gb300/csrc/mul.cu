@@ -1245,7 +1245,7 @@ struct F32Variant {
   int tt, mr, mc, km;  // tile edge, lane micro-tile, largest lambda extent of one stage
   int panel;           // 0: one tile per warp; P > 0: row panels of up to P tiles per warp
   int nt;              // K-major kernel with bulk-copy staging (mul_nt.cu), micro-tile per tile:
-                       // 1 = looped 4-wide steps, 2 = full 20-wide pieces unrolled
+                       // 1 = runtime row pitch, 2 = compile-time pitch for full 20-wide pieces
 };
 constexpr F32Variant kF32Variants[] = {{20, 0, 0, 20, 0, 1},  {20, 0, 0, 20, 0, 2},  {20, 4, 4, 20, 0, 0},
                                        {20, 4, 4, 40, 0, 0},  {16, 4, 2, 32, 0, 0},  {12, 3, 2, 36, 0, 0},

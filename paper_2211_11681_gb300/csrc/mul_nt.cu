@@ -195,10 +195,10 @@ __device__ __forceinline__ void nt_issue(const NtArgs& a, const NtChunk& c0, con
   const uint32_t bytes = (uint32_t)((TH + TW) * 4 * ((v0 ? c0.kc : 0) + (v1 ? c1.kc : 0)));
   const int n0 = v0 ? (c0.kc == c0.nlp ? 2 : TH + TW) : 0;
   const int n1 = v1 ? (c1.kc == c1.nlp ? 2 : TH + TW) : 0;
-  asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");  // earlier reads of buf before the copies
-  __syncwarp();
+  // (the caller's __syncwarp ends every read of buf before this point)
   if (lane == 0) nt_expect(bar, bytes);
   __syncwarp();
+  if (lane < n0 + n1) asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
   for (int j = lane; j < n0 + n1; j += 32) {
     const int h = j < n0 ? 0 : 1;
     const int q = h ? j - n0 : j;
@@ -219,7 +219,7 @@ __device__ __forceinline__ void nt_issue(const NtArgs& a, const NtChunk& c0, con
 
 template <int MR, int MC, int KC>
 __device__ __forceinline__ void nt_fma_fixed(const float* xs, const float* ys, float* p) {
-#pragma unroll
+#pragma unroll 1
   for (int t = 0; t < KC; t += 4) {
     float4 xv[MR];
 #pragma unroll
@@ -241,11 +241,11 @@ __device__ __forceinline__ void nt_fma_fixed(const float* xs, const float* ys, f
 }
 
 // The FMAs of one staged piece: MR rows of the X slice and MC rows of the Y slice (row pitch
-// kc), 4 values of t per step.  The full 20-wide piece, the common case, is unrolled with
-// constant offsets.
-template <int MR, int MC, bool UNROLL>
+// kc), 4 values of t per step.  With CONST the full 20-wide piece, the common case, runs with
+// a compile-time row pitch (one address per step, constant offsets for the rows).
+template <int MR, int MC, bool CONST>
 __device__ __forceinline__ void nt_fma_chunk(const float* xs, const float* ys, int kc, float* p) {
-  if (UNROLL && kc == kNtKC) {
+  if (CONST && kc == kNtKC) {
     nt_fma_fixed<MR, MC, kNtKC>(xs, ys, p);
     return;
   }
@@ -279,7 +279,7 @@ __device__ __forceinline__ void nt_fold(float& acc, float& p) {
 }
 
 // One output tile whose padded extent is 4MR x 4MC.  Returns false on a time-out.
-template <int MR, int MC, bool UNROLL>
+template <int MR, int MC, bool CONST>
 __device__ bool nt_tile(const NtArgs& a, const Tile& tile, int k, int nu, int nup, int ni, int nj, float* wbase,
                         uint64_t* bars, NtEntry* ent, uint32_t& phase, int lane) {
   constexpr int TH = 4 * MR, TW = 4 * MC, NQ = MR * MC;
@@ -325,7 +325,7 @@ __device__ bool nt_tile(const NtArgs& a, const Tile& tile, int k, int nu, int nu
       }
       if (last >= 0) {
         const float* hb = wbase + buf * kNtBuf + half * kNtHalf;
-        nt_fma_chunk<MR, MC, UNROLL>(hb + mr * MR * kc, hb + kNtRegion + mc * MC * kc, kc, p);
+        nt_fma_chunk<MR, MC, CONST>(hb + mr * MR * kc, hb + kNtRegion + mc * MC * kc, kc, p);
         if (last && ++folded == kNtFold) {
           folded = 0;
 #pragma unroll
@@ -356,7 +356,7 @@ __device__ bool nt_tile(const NtArgs& a, const Tile& tile, int k, int nu, int nu
   return ok;
 }
 
-template <bool UNROLL>
+template <bool CONST>
 __global__ void __launch_bounds__(kNtWarps * 32, 4) mul_f32_nt_kernel(NtArgs a) {
   extern __shared__ __align__(128) float nsm[];  // [warp][buffer][kNtBuf]
   __shared__ __align__(8) uint64_t bars[kNtWarps][2];
@@ -385,7 +385,7 @@ __global__ void __launch_bounds__(kNtWarps * 32, 4) mul_f32_nt_kernel(NtArgs a) 
     uint64_t* bw = bars[w];
     NtEntry* en = sent[w];
 #define SF_NT_CASE(R, Cc) \
-  case (R - 1) * 5 + (Cc - 1): ok = nt_tile<R, Cc, UNROLL>(a, tile, k, nu, nup, ni, nj, wb, bw, en, phase, lane); break;
+  case (R - 1) * 5 + (Cc - 1): ok = nt_tile<R, Cc, CONST>(a, tile, k, nu, nup, ni, nj, wb, bw, en, phase, lane); break;
     switch ((mr - 1) * 5 + (mc - 1)) {
       SF_NT_CASE(1, 1) SF_NT_CASE(1, 2) SF_NT_CASE(1, 3) SF_NT_CASE(1, 4) SF_NT_CASE(1, 5)
       SF_NT_CASE(2, 1) SF_NT_CASE(2, 2) SF_NT_CASE(2, 3) SF_NT_CASE(2, 4) SF_NT_CASE(2, 5)
@@ -507,7 +507,18 @@ s_status nt_configure(MulDesc* d, bool x_trans, bool y_trans, bool y_sym) {
     yl = Side{py.colptr, py.rowidx, py.cscblk, py.voff, true};
     ytrans = true;
   }
-  if ((st = nt_side(d->py, yl, ytrans, &d->nty))) return st;
+  if (y_sym && !x_trans && d->ntx.prep) {
+    // B = A read through A's rows: the same padded blocks as the X side, one copy for both
+    nt_free_side(&d->nty);
+    d->nty.ptr = yl.ptr;
+    d->nty.idx = yl.idx;
+    d->nty.blk = yl.blk;
+    d->nty.pat = d->py;
+    d->nty.off = d->ntx.off;
+    d->nty.from_x = true;
+  } else if ((st = nt_side(d->py, yl, ytrans, &d->nty))) {
+    return st;
+  }
   d->nt_ysym = y_sym;
   return S_OK;
 }
@@ -526,13 +537,13 @@ bool nt_usable(const MulDesc& d, const void* X, const void* Y) {
   if (!d.ntx.off || !d.nty.off) return false;
   // bulk copies read 16-byte aligned sources
   if (!d.ntx.prep && (reinterpret_cast<uintptr_t>(X) & 15)) return false;
-  if (!d.nty.prep && (reinterpret_cast<uintptr_t>(Y) & 15)) return false;
+  if (!d.nty.prep && !d.nty.from_x && (reinterpret_cast<uintptr_t>(Y) & 15)) return false;
   // a symmetric Y side reads B through A's rows: only valid for B = A
   if (d.nt_ysym && X != Y) return false;
   return true;
 }
 
-s_status launch_nt(const MulDesc& d, const void* X, const void* Y, void* C, cudaStream_t st, bool unroll) {
+s_status launch_nt(const MulDesc& d, const void* X, const void* Y, void* C, cudaStream_t st, bool const_pitch) {
   if (d.ntiles == 0) return S_OK;
   s_status s = take_timeout(d);
   if (s) return s;
@@ -542,7 +553,9 @@ s_status launch_nt(const MulDesc& d, const void* X, const void* Y, void* C, cuda
     if ((s = nt_prepare(d.ntx, (const float*)X, st))) return s;
     xb = d.ntx.scratch;
   }
-  if (d.nty.prep) {
+  if (d.nty.from_x) {
+    yb = xb;
+  } else if (d.nty.prep) {
     if ((s = nt_prepare(d.nty, (const float*)Y, st))) return s;
     yb = d.nty.scratch;
   }
@@ -567,7 +580,7 @@ s_status launch_nt(const MulDesc& d, const void* X, const void* Y, void* C, cuda
   a.err = d.err;
   a.C = (float*)C;
   SF_CUDA(cudaMemsetAsync(d.counter, 0, sizeof(unsigned int), st));
-  void (*kern)(NtArgs) = unroll ? mul_f32_nt_kernel<true> : mul_f32_nt_kernel<false>;
+  void (*kern)(NtArgs) = const_pitch ? mul_f32_nt_kernel<true> : mul_f32_nt_kernel<false>;
   SF_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kNtSmem));
   int per_sm = 0;
   SF_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kNtWarps * 32, kNtSmem));
