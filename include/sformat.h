@@ -46,7 +46,7 @@ typedef enum {
   S_ERR_MISMATCH = -3,      /* operands from different trees / incompatible patterns  */
   S_ERR_NOMEM = -4,         /* device or host allocation failed                       */
   S_ERR_CUDA = -5,          /* a CUDA call failed; see s_last_error()                 */
-  S_ERR_NOT_CONVERGED = -6, /* Newton-Schulz residual grew over two consecutive steps */
+  S_ERR_NOT_CONVERGED = -6, /* Newton-Schulz iteration diverged (see s_funm)          */
   S_ERR_TIMEOUT = -7        /* a bounded device-side wait ran out                     */
 } s_status;
 
@@ -245,7 +245,8 @@ typedef struct {
  * its diagonal blocks).  A and F are double device buffers.
  *   S_SQRT     A^{1/2} by coupled Newton-Schulz: Y_0 = A/c, Z_0 = I,
  *              T_k = (3I - P_S(Z_k Y_k))/2, Y_{k+1} = P_S(Y_k T_k), Z_{k+1} = P_S(T_k Z_k),
- *              F = sqrt(c) Y_steps.
+ *              F = sqrt(c) Y_steps.  S_ERR_NOT_CONVERGED when ||T_k - I||_F is not finite, or
+ *              grew by more than 1.5x on two consecutive steps while above 1e-3 of ||T_0 - I||_F.
  *   S_EXP, S_EXP_NEG   exp(+-A) by the power series of Sec. 4.4 truncated at the Taylor
  *              degree, Horner's rule on X = +-A/2^s, then s masked squarings,
  *              s = max(0, ceil(log2(lambda/0.5))).  With prec S_FP32 the Horner products

@@ -173,6 +173,12 @@ struct NtLister {
     c.yo = en.yo;
     c.nlp = en.nlp;
     c.t0 = t0;
+    if (t0 == 0 && en.nlp <= kNtKC) {  // the common case: the whole block in one piece
+      c.kc = en.nlp;
+      c.last = 1;
+      ++e;
+      return c;
+    }
     c.kc = min(kNtKC, en.nlp - t0);
     c.last = t0 + c.kc >= en.nlp ? 1 : 0;
     if (c.last) {
@@ -192,6 +198,21 @@ template <int TH, int TW>
 __device__ __forceinline__ void nt_issue(const NtArgs& a, const NtChunk& c0, const NtChunk& c1, float* buf,
                                          uint64_t* bar, int lane) {
   const bool v0 = c0.last >= 0, v1 = c1.last >= 0;
+  if ((!v0 || c0.kc == c0.nlp) && (!v1 || c1.kc == c1.nlp)) {
+    // whole blocks: lane 2h + o copies operand o (X, Y) of half-warp h's piece
+    if (lane == 0) nt_expect(bar, (uint32_t)((TH + TW) * 4 * ((v0 ? c0.kc : 0) + (v1 ? c1.kc : 0))));
+    __syncwarp();
+    if (lane < 4) {
+      const int h = lane >> 1, o = lane & 1;
+      const NtChunk& c = h ? c1 : c0;
+      if (h ? v1 : v0) {
+        asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+        nt_bulk(buf + h * kNtHalf + o * kNtRegion, o ? a.Y + c.yo : a.X + c.xo, (uint32_t)((o ? TW : TH) * c.nlp * 4),
+                bar);
+      }
+    }
+    return;
+  }
   const uint32_t bytes = (uint32_t)((TH + TW) * 4 * ((v0 ? c0.kc : 0) + (v1 ? c1.kc : 0)));
   const int n0 = v0 ? (c0.kc == c0.nlp ? 2 : TH + TW) : 0;
   const int n1 = v1 ? (c1.kc == c1.nlp ? 2 : TH + TW) : 0;
