@@ -447,6 +447,14 @@ def run_grad(args, rank, world):
     out = {}
     for prec in [p_ for p_ in args.precisions.split(",") if p_ in ("fp32", "fp64")]:
         torch.cuda.synchronize()
+        torch.cuda.empty_cache()
+        ck_bytes = 2 * steps * pat.nnz * (4 if prec == "fp32" else 8)
+        free, _ = torch.cuda.mem_get_info()
+        if ck_bytes + 8 * pat.nnz * 8 > free:     # checkpoints + about eight work matrices
+            out[prec] = {"skipped": "the %.0f GB of checkpoints and work buffers exceed the %.0f GB of free device "
+                                    "memory" % ((ck_bytes + 64 * pat.nnz) / 1e9, free / 1e9),
+                         "checkpoint_gb": round(ck_bytes / 1e9, 2)}
+            continue
         Ar = A.clone().requires_grad_(True)
         t1 = time.time()
         X = SqrtmNS.apply(Ar, pat, steps, c, prec)
@@ -464,7 +472,7 @@ def run_grad(args, rank, world):
                      "checkpoint_gb": round(2 * steps * pat.nnz * (4 if prec == "fp32" else 8) / 1e9, 2)}
         del Ar, X, L
         torch.cuda.empty_cache()
-    if "fp32" in out and "fp64" in out:
+    if "dloss_dell" in out.get("fp32", {}) and "dloss_dell" in out.get("fp64", {}):
         out["fp32"]["dloss_dell_rel_vs_fp64"] = abs(out["fp32"]["dloss_dell"] / out["fp64"]["dloss_dell"] - 1)
     line = {"metric": "d/dell of z^T P_S(A(ell)^{1/2}) z through %d Newton-Schulz steps" % steps,
             "value": out.get("fp32", {}).get("backward_s"), "unit": "s per reverse pass (mixed)",

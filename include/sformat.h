@@ -116,12 +116,14 @@ s_status s_plan_create(s_pattern A, s_pattern B, s_pattern C, s_prec prec, s_pla
 s_status s_plan_destroy(s_plan plan);
 /* Exact triple count and useful flop count of the plan's product. */
 s_status s_plan_stats(s_plan plan, int64_t* triples, double* flops);
-/* Autotuner of S_FP32 and S_FP64_DF plans: times every kernel variant of the plan's
+/* Autotuner of S_FP32 and S_FP64_DF plans: times the kernel variants of the plan's
  * arithmetic (output tile edge, the micro-tile of one lane, for float also the lambda extent
- * of a stage) on the given operands, three launches each after one warm-up, and keeps the
- * fastest for this plan's forward product.  C is overwritten.  *chosen (optional) receives
- * the variant index.  S_FP64, S_BF16X3 and S_TF32X3 plans have one shape (no-op).
- * Synchronises the stream. */
+ * of a stage) on the given operands and keeps the fastest for this plan's forward product.
+ * Each variant runs one timed warm-up launch; one more than twice as slow as the best so far
+ * stops there, the others are timed over three more launches.  Float tile and row-panel
+ * shapes narrower than the root-mean-square block edge of S_C are skipped.  C is
+ * overwritten.  *chosen (optional) receives the variant index.  S_FP64, S_BF16X3 and
+ * S_TF32X3 plans have one shape (no-op).  Synchronises the stream. */
 s_status s_plan_autotune(s_plan plan, const void* A, const void* B, void* C, void* stream, int* chosen);
 /* Selects kernel variant `variant` (0 .. s_plan_num_variants_of(plan)-1) for the plan's
  * forward product by hand (S_FP32 and S_FP64_DF plans). */
@@ -146,7 +148,8 @@ s_status s_plan_set_symmetric_a(s_plan plan, int symmetric);
  * lambda blocks are packed into one stage up to this extent).  Float variants 0 (the default)
  * and 1 are the K-major kernel: each lambda block staged by one bulk copy, the micro-tile a
  * quarter of each tile's padded edge (reported as 0 x 0), lambda staged in pieces of at most
- * 20; variant 1 addresses full 20-wide pieces with a compile-time row pitch.  For an S_TF32X3 plan: 32 rows
+ * 20; variant 1 multiplies with packed two-lane FMAs (partial sums of even and odd lambda
+ * values kept apart).  For an S_TF32X3 plan: 32 rows
  * of a panel, 128 MMA rows (member columns), 32 MMA columns, lambda extent 24 per stage.
  * Any output may be NULL. */
 s_status s_plan_variant(s_plan plan, int variant, int* tile, int* micro_rows, int* micro_cols, int* stage_k);
