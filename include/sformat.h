@@ -148,8 +148,7 @@ s_status s_plan_set_symmetric_a(s_plan plan, int symmetric);
  * lambda blocks are packed into one stage up to this extent).  Float variants 0 (the default)
  * and 1 are the K-major kernel: each lambda block staged by one bulk copy, the micro-tile a
  * quarter of each tile's padded edge (reported as 0 x 0), lambda staged in pieces of at most
- * 20; variant 1 multiplies with packed two-lane FMAs (partial sums of even and odd lambda
- * values kept apart).  For an S_TF32X3 plan: 32 rows
+ * 20; variant 1 addresses full 20-wide pieces with a compile-time row pitch.  For an S_TF32X3 plan: 32 rows
  * of a panel, 128 MMA rows (member columns), 32 MMA columns, lambda extent 24 per stage.
  * Any output may be NULL. */
 s_status s_plan_variant(s_plan plan, int variant, int* tile, int* micro_rows, int* micro_cols, int* stage_k);

@@ -155,7 +155,7 @@ s_status take_timeout(const MulDesc& d);
 // with these buffers can use it, the launch, and the release of its scratch.
 s_status nt_configure(MulDesc* d, bool x_trans, bool y_trans, bool y_sym);
 bool nt_usable(const MulDesc& d, const void* X, const void* Y);
-s_status launch_nt(const MulDesc& d, const void* X, const void* Y, void* C, cudaStream_t st, int form);
+s_status launch_nt(const MulDesc& d, const void* X, const void* Y, void* C, cudaStream_t st, bool const_pitch);
 void nt_free_side(NtSideDesc* s);
 s_status run_mul(const MulDesc& d, s_prec prec, const void* X, const void* Y, void* C, cudaStream_t st);
 

@@ -1245,16 +1245,14 @@ struct F32Variant {
   int tt, mr, mc, km;  // tile edge, lane micro-tile, largest lambda extent of one stage
   int panel;           // 0: one tile per warp; P > 0: row panels of up to P tiles per warp
   int nt;              // K-major kernel with bulk-copy staging (mul_nt.cu), micro-tile per tile:
-                       // 1 = one FMA per product, 2 = packed two-lane FMAs, 3 and 4 = the same
-                       // with two pieces per half-warp and stage
+                       // 1 = runtime row pitch, 2 = compile-time pitch for full 20-wide pieces
 };
-constexpr F32Variant kF32Variants[] = {{20, 0, 0, 20, 0, 1},  {20, 0, 0, 20, 0, 2},  {20, 0, 0, 40, 0, 3},
-                                       {20, 0, 0, 40, 0, 4},  {20, 4, 4, 20, 0, 0},  {20, 4, 4, 40, 0, 0},
-                                       {16, 4, 2, 32, 0, 0},  {12, 3, 2, 36, 0, 0},  {10, 2, 2, 40, 0, 0},
-                                       {8, 2, 1, 32, 0, 0},   {12, 3, 2, 12, 3, 0},  {10, 2, 2, 10, 4, 0},
-                                       {8, 2, 1, 8, 4, 0}};
-constexpr int kNumF32Variants = 13;
-constexpr int kF32Fallback = 4;  // tile kernel of the K-major variants' tile list, for unaligned buffers
+constexpr F32Variant kF32Variants[] = {{20, 0, 0, 20, 0, 1},  {20, 0, 0, 20, 0, 2},  {20, 4, 4, 20, 0, 0},
+                                       {20, 4, 4, 40, 0, 0},  {16, 4, 2, 32, 0, 0},  {12, 3, 2, 36, 0, 0},
+                                       {10, 2, 2, 40, 0, 0},  {8, 2, 1, 32, 0, 0},   {12, 3, 2, 12, 3, 0},
+                                       {10, 2, 2, 10, 4, 0},  {8, 2, 1, 8, 4, 0}};
+constexpr int kNumF32Variants = 11;
+constexpr int kF32Fallback = 2;  // tile kernel of the K-major variants' tile list, for unaligned buffers
 
 static int num_sms() { return sm_count(); }
 
@@ -1430,12 +1428,12 @@ static F32PanelKernel f32_panel_kernel(bool tx, bool ty) {
 
 static F32Kernel f32_kernel_of(int v, bool tx, bool ty) {
   switch (v) {
+    case 3: return f32_kernel<3>(tx, ty);
+    case 4: return f32_kernel<4>(tx, ty);
     case 5: return f32_kernel<5>(tx, ty);
     case 6: return f32_kernel<6>(tx, ty);
     case 7: return f32_kernel<7>(tx, ty);
-    case 8: return f32_kernel<8>(tx, ty);
-    case 9: return f32_kernel<9>(tx, ty);
-    default: return f32_kernel<4>(tx, ty);
+    default: return f32_kernel<2>(tx, ty);
   }
 }
 
@@ -1461,9 +1459,9 @@ static s_status launch_f32_panel(const MulDesc& d, const void* X, const void* Y,
   a.ntiles = d.ntiles;
   a.counter = d.counter;
   SF_CUDA(cudaMemsetAsync(d.counter, 0, sizeof(unsigned int), st));
-  F32PanelKernel kern = d.variant == 10   ? f32_panel_kernel<10>(d.x.trans, d.y.trans)
-                        : d.variant == 11 ? f32_panel_kernel<11>(d.x.trans, d.y.trans)
-                                          : f32_panel_kernel<12>(d.x.trans, d.y.trans);
+  F32PanelKernel kern = d.variant == 8   ? f32_panel_kernel<8>(d.x.trans, d.y.trans)
+                        : d.variant == 9 ? f32_panel_kernel<9>(d.x.trans, d.y.trans)
+                                         : f32_panel_kernel<10>(d.x.trans, d.y.trans);
   const size_t smem = f32_smem(d.variant);
   SF_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   int per_sm = 0;
@@ -1501,7 +1499,7 @@ static s_status launch_typed(const MulDesc& d, const void* X, const void* Y, voi
     if (d.edge != kF32Variants[d.variant].tt) return set_error(S_ERR_ARG, "internal: tile list does not match variant");
     int v = d.variant;
     if (kF32Variants[v].nt) {
-      if (nt_usable(d, X, Y)) return launch_nt(d, X, Y, C, st, kF32Variants[v].nt);
+      if (nt_usable(d, X, Y)) return launch_nt(d, X, Y, C, st, kF32Variants[v].nt == 2);
       v = kF32Fallback;  // same tile list (edge 20); reads any alignment
     }
     kern = f32_kernel_of(v, d.x.trans, d.y.trans);

@@ -15,8 +15,7 @@
 // of MR x MC micro-tiles; each half-warp (16 lanes) holds the whole grid, and the two halves
 // take alternate lambda blocks of the tile's intersection list (split-K), so all 32 lanes
 // work whatever the block widths.  A lane's step over 4 values of t is MR + MC 16-byte
-// shared loads and 4 MR MC fused multiply-adds (or 2 MR MC packed two-lane ones, which keep
-// the partial sums of even and odd t apart).  Each lambda block's partial sum is kept in
+// shared loads and 4 MR MC fused multiply-adds.  Each lambda block's partial sum is kept in
 // a float register per entry and folded into the running sum with an error-free two-sum
 // every kNtFold blocks, the rounding error carried in the partial; at the end the two
 // halves' sums are combined the same way.  The summation order is fixed (deterministic).
@@ -37,15 +36,10 @@ constexpr int kNtWarps = 4;
 constexpr int kNtKC = 20;                        // lambda values per staged chunk
 constexpr int kNtEnt = 32;                       // matching lambda blocks listed at once
 constexpr int kNtRegion = 20 * kNtKC;            // floats of one operand slice (<= 20 rows)
+constexpr int kNtHalf = 2 * kNtRegion + 16;      // X | Y of one half-warp, + 64-byte bank shift
+constexpr int kNtBuf = 2 * kNtHalf;              // one stage buffer: both halves
 constexpr int kNtFold = 4;                       // lambda blocks per two-sum fold
-// A stage buffer holds PPH pieces per half-warp: [half][slot][X | Y], the second half shifted by
-// 16 banks.  Two buffers per warp.
-template <int PPH>
-struct NtShape {
-  static constexpr int kHalf = PPH * 2 * kNtRegion + 16;  // floats of one half-warp's slots
-  static constexpr int kBuf = 2 * kHalf;                  // floats of one stage buffer
-  static constexpr size_t kSmem = sizeof(float) * kNtWarps * 2 * kBuf;
-};
+constexpr size_t kNtSmem = sizeof(float) * kNtWarps * 2 * kNtBuf;
 
 struct NtEntry {
   int64_t xo, yo;  // float offsets of the X and Y slices (rows r0.. / columns c0..)
@@ -197,69 +191,85 @@ struct NtLister {
   }
 };
 
-// Issue the copies of one stage into `buf`, completing on `bar`: piece p of c[0 .. 2 PPH) goes
-// to half-warp p & 1, slot p >> 1.  A whole lambda block moves as one copy per operand (its
-// rows r0.. / columns c0.. are contiguous); a piece of a wider block as one copy per row.
-// The pieces of one stage (all lanes hold the same values).
-template <int NP>
-struct NtStage {
-  NtChunk c[NP];
-};
-
-template <int TH, int TW, int PPH>
-__device__ __forceinline__ void nt_issue(const NtArgs& a, const NtStage<2 * PPH> sg, float* buf, uint64_t* bar,
-                                         int lane) {
-  constexpr int NP = 2 * PPH;
-  uint32_t bytes = 0;
-  bool whole = true;
-#pragma unroll
-  for (int p = 0; p < NP; ++p)
-    if (sg.c[p].last >= 0) {
-      bytes += (uint32_t)((TH + TW) * 4 * sg.c[p].kc);
-      whole = whole && sg.c[p].kc == sg.c[p].nlp;
-    }
-  // (the caller's __syncwarp ends every read of buf before this point)
-  if (lane == 0) nt_expect(bar, bytes);
-  __syncwarp();
-  if (whole) {
-    // lane 2p + o copies operand o (X, Y) of piece p
-#pragma unroll
-    for (int p = 0; p < NP; ++p) {
-      if ((lane >> 1) == p && sg.c[p].last >= 0) {
-        const int o = lane & 1;
+// Issue the copies of one stage (piece c0 for half-warp 0, c1 for half-warp 1) into `buf`,
+// completing on `bar`.  A whole lambda block moves as one copy per operand (its rows r0.. /
+// columns c0.. are contiguous); a piece of a wider block as one copy per row.
+template <int TH, int TW>
+__device__ __forceinline__ void nt_issue(const NtArgs& a, const NtChunk& c0, const NtChunk& c1, float* buf,
+                                         uint64_t* bar, int lane) {
+  const bool v0 = c0.last >= 0, v1 = c1.last >= 0;
+  if ((!v0 || c0.kc == c0.nlp) && (!v1 || c1.kc == c1.nlp)) {
+    // whole blocks: lane 2h + o copies operand o (X, Y) of half-warp h's piece
+    if (lane == 0) nt_expect(bar, (uint32_t)((TH + TW) * 4 * ((v0 ? c0.kc : 0) + (v1 ? c1.kc : 0))));
+    __syncwarp();
+    if (lane < 4) {
+      const int h = lane >> 1, o = lane & 1;
+      const NtChunk& c = h ? c1 : c0;
+      if (h ? v1 : v0) {
         asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
-        nt_bulk(buf + (p & 1) * NtShape<PPH>::kHalf + (p >> 1) * 2 * kNtRegion + o * kNtRegion,
-                o ? a.Y + sg.c[p].yo : a.X + sg.c[p].xo, (uint32_t)((o ? TW : TH) * sg.c[p].nlp * 4), bar);
+        nt_bulk(buf + h * kNtHalf + o * kNtRegion, o ? a.Y + c.yo : a.X + c.xo, (uint32_t)((o ? TW : TH) * c.nlp * 4),
+                bar);
       }
     }
     return;
   }
-  // pieces of wider blocks: one copy per row, TH + TW per piece; lanes take copies in turn
-  asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
-#pragma unroll
-  for (int p = 0; p < NP; ++p) {
-    if (sg.c[p].last < 0) continue;
-    float* dst = buf + (p & 1) * NtShape<PPH>::kHalf + (p >> 1) * 2 * kNtRegion;
-    const NtChunk cp = sg.c[p];
-    if (cp.kc == cp.nlp) {
-      if (lane == 0) nt_bulk(dst, a.X + cp.xo, (uint32_t)(TH * cp.nlp * 4), bar);
-      if (lane == 1) nt_bulk(dst + kNtRegion, a.Y + cp.yo, (uint32_t)(TW * cp.nlp * 4), bar);
+  const uint32_t bytes = (uint32_t)((TH + TW) * 4 * ((v0 ? c0.kc : 0) + (v1 ? c1.kc : 0)));
+  const int n0 = v0 ? (c0.kc == c0.nlp ? 2 : TH + TW) : 0;
+  const int n1 = v1 ? (c1.kc == c1.nlp ? 2 : TH + TW) : 0;
+  // (the caller's __syncwarp ends every read of buf before this point)
+  if (lane == 0) nt_expect(bar, bytes);
+  __syncwarp();
+  if (lane < n0 + n1) asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+  for (int j = lane; j < n0 + n1; j += 32) {
+    const int h = j < n0 ? 0 : 1;
+    const int q = h ? j - n0 : j;
+    const NtChunk& c = h ? c1 : c0;
+    const int nq = h ? n1 : n0;
+    float* dst = buf + h * kNtHalf;
+    if (nq == 2) {
+      if (q == 0) nt_bulk(dst, a.X + c.xo, (uint32_t)(TH * c.nlp * 4), bar);
+      else nt_bulk(dst + kNtRegion, a.Y + c.yo, (uint32_t)(TW * c.nlp * 4), bar);
+    } else if (q < TH) {
+      nt_bulk(dst + q * c.kc, a.X + c.xo + (int64_t)q * c.nlp + c.t0, (uint32_t)(c.kc * 4), bar);
     } else {
-      for (int q = lane; q < TH + TW; q += 32) {
-        if (q < TH)
-          nt_bulk(dst + q * cp.kc, a.X + cp.xo + (int64_t)q * cp.nlp + cp.t0, (uint32_t)(cp.kc * 4), bar);
-        else
-          nt_bulk(dst + kNtRegion + (q - TH) * cp.kc, a.Y + cp.yo + (int64_t)(q - TH) * cp.nlp + cp.t0,
-                  (uint32_t)(cp.kc * 4), bar);
+      const int r = q - TH;
+      nt_bulk(dst + kNtRegion + r * c.kc, a.Y + c.yo + (int64_t)r * c.nlp + c.t0, (uint32_t)(c.kc * 4), bar);
+    }
+  }
+}
+
+template <int MR, int MC, int KC>
+__device__ __forceinline__ void nt_fma_fixed(const float* xs, const float* ys, float* p) {
+#pragma unroll 1
+  for (int t = 0; t < KC; t += 4) {
+    float4 xv[MR];
+#pragma unroll
+    for (int i = 0; i < MR; ++i) xv[i] = *reinterpret_cast<const float4*>(xs + i * KC + t);
+#pragma unroll
+    for (int j = 0; j < MC; ++j) {
+      const float4 yv = *reinterpret_cast<const float4*>(ys + j * KC + t);
+#pragma unroll
+      for (int i = 0; i < MR; ++i) {
+        float s = p[i * MC + j];
+        s = fmaf(xv[i].x, yv.x, s);
+        s = fmaf(xv[i].y, yv.y, s);
+        s = fmaf(xv[i].z, yv.z, s);
+        s = fmaf(xv[i].w, yv.w, s);
+        p[i * MC + j] = s;
       }
     }
   }
 }
 
 // The FMAs of one staged piece: MR rows of the X slice and MC rows of the Y slice (row pitch
-// kc), 4 values of t per step, one fused multiply-add per product into p[.].x.
-template <int MR, int MC>
-__device__ __forceinline__ void nt_fma_chunk(const float* xs, const float* ys, int kc, float2* p) {
+// kc), 4 values of t per step.  With CONST the full 20-wide piece, the common case, runs with
+// a compile-time row pitch (one address per step, constant offsets for the rows).
+template <int MR, int MC, bool CONST>
+__device__ __forceinline__ void nt_fma_chunk(const float* xs, const float* ys, int kc, float* p) {
+  if (CONST && kc == kNtKC) {
+    nt_fma_fixed<MR, MC, kNtKC>(xs, ys, p);
+    return;
+  }
   for (int t = 0; t < kc; t += 4) {
     float4 xv[MR];
 #pragma unroll
@@ -269,33 +279,11 @@ __device__ __forceinline__ void nt_fma_chunk(const float* xs, const float* ys, i
       const float4 yv = *reinterpret_cast<const float4*>(ys + j * kc + t);
 #pragma unroll
       for (int i = 0; i < MR; ++i) {
-        float s = p[i * MC + j].x;
+        float s = p[i * MC + j];
         s = fmaf(xv[i].x, yv.x, s);
         s = fmaf(xv[i].y, yv.y, s);
         s = fmaf(xv[i].z, yv.z, s);
         s = fmaf(xv[i].w, yv.w, s);
-        p[i * MC + j].x = s;
-      }
-    }
-  }
-}
-
-// The same with packed two-lane FMAs (two products per instruction): every entry keeps two
-// partial sums, of the even and of the odd values of t, added when the partial is folded.
-template <int MR, int MC>
-__device__ __forceinline__ void nt_fma2_chunk(const float* xs, const float* ys, int kc, float2* p) {
-  for (int t = 0; t < kc; t += 4) {
-    float4 xv[MR];
-#pragma unroll
-    for (int i = 0; i < MR; ++i) xv[i] = *reinterpret_cast<const float4*>(xs + i * kc + t);
-#pragma unroll
-    for (int j = 0; j < MC; ++j) {
-      const float4 yv = *reinterpret_cast<const float4*>(ys + j * kc + t);
-#pragma unroll
-      for (int i = 0; i < MR; ++i) {
-        float2 s = p[i * MC + j];
-        s = __ffma2_rn(make_float2(xv[i].x, xv[i].y), make_float2(yv.x, yv.y), s);
-        s = __ffma2_rn(make_float2(xv[i].z, xv[i].w), make_float2(yv.z, yv.w), s);
         p[i * MC + j] = s;
       }
     }
@@ -312,21 +300,16 @@ __device__ __forceinline__ void nt_fold(float& acc, float& p) {
 }
 
 // One output tile whose padded extent is 4MR x 4MC.  Returns false on a time-out.
-template <int MR, int MC, bool PAIR, int PPH>
+template <int MR, int MC, bool CONST>
 __device__ bool nt_tile(const NtArgs& a, const Tile& tile, int k, int nu, int nup, int ni, int nj, float* wbase,
                         uint64_t* bars, NtEntry* ent, uint32_t& phase, int lane) {
-  constexpr int TH = 4 * MR, TW = 4 * MC, NQ = MR * MC, NP = 2 * PPH;
-  using Sh = NtShape<PPH>;
+  constexpr int TH = 4 * MR, TW = 4 * MC, NQ = MR * MC;
   const int half = lane >> 4, hl = lane & 15;
   const int mr = hl >> 2, mc = hl & 3;
   const int th = min(20, ni - tile.r0), tw = min(20, nj - tile.c0);
-  float acc[NQ];
-  float2 p[NQ];  // partial sums: in .x (one FMA per product), or of even / odd t in .x / .y (PAIR)
+  float acc[NQ], p[NQ];
 #pragma unroll
-  for (int q = 0; q < NQ; ++q) {
-    acc[q] = 0.0f;
-    p[q] = make_float2(0.0f, 0.0f);
-  }
+  for (int q = 0; q < NQ; ++q) acc[q] = p[q] = 0.0f;
   int folded = 0;
   bool ok = true;
   NtLister L;
@@ -340,97 +323,67 @@ __device__ bool nt_tile(const NtArgs& a, const Tile& tile, int k, int nu, int nu
   L.c0 = tile.c0;
   L.nm = L.e = L.t0 = 0;
   int buf = 0;
-  int kc[PPH], last[PPH];  // this half-warp's pieces of the stage in `buf` (last < 0: none)
-  bool any;
   {
-    NtStage<NP> c;
-#pragma unroll
-    for (int q = 0; q < NP; ++q) c.c[q] = L.next(lane);
-#pragma unroll
-    for (int s2 = 0; s2 < PPH; ++s2) {
-      kc[s2] = half ? c.c[2 * s2 + 1].kc : c.c[2 * s2].kc;
-      last[s2] = half ? c.c[2 * s2 + 1].last : c.c[2 * s2].last;
-    }
-    any = c.c[0].last >= 0;
-    if (any) nt_issue<TH, TW, PPH>(a, c, wbase, bars, lane);
-  }
-  while (any) {
-    bool more;
-    int nkc[PPH], nlast[PPH];
-    {
-      NtStage<NP> n;
-#pragma unroll
-      for (int q = 0; q < NP; ++q) n.c[q] = L.next(lane);
-      more = n.c[0].last >= 0;
-      if (more) nt_issue<TH, TW, PPH>(a, n, wbase + (buf ^ 1) * Sh::kBuf, bars + (buf ^ 1), lane);
-#pragma unroll
-      for (int s2 = 0; s2 < PPH; ++s2) {
-        nkc[s2] = half ? n.c[2 * s2 + 1].kc : n.c[2 * s2].kc;
-        nlast[s2] = half ? n.c[2 * s2 + 1].last : n.c[2 * s2].last;
+    const NtChunk c0 = L.next(lane);
+    const NtChunk c1 = L.next(lane);
+    int kc = half ? c1.kc : c0.kc;
+    int last = half ? c1.last : c0.last;
+    if (c0.last >= 0) nt_issue<TH, TW>(a, c0, c1, wbase, bars, lane);
+    while (c0.last >= 0) {
+      const NtChunk n0 = L.next(lane);
+      const NtChunk n1 = L.next(lane);
+      const bool more = n0.last >= 0;
+      if (more) nt_issue<TH, TW>(a, n0, n1, wbase + (buf ^ 1) * kNtBuf, bars + (buf ^ 1), lane);
+      const bool got = nt_wait(bars + buf, (phase >> buf) & 1u);
+      phase ^= 1u << buf;
+      if (!__all_sync(0xffffffffu, got)) {
+        ok = false;
+        if (more) {  // let the copies already issued land before the warp leaves
+          nt_wait(bars + (buf ^ 1), (phase >> (buf ^ 1)) & 1u);
+          phase ^= 1u << (buf ^ 1);
+        }
+        break;
       }
-    }
-    const bool got = nt_wait(bars + buf, (phase >> buf) & 1u);
-    phase ^= 1u << buf;
-    if (!__all_sync(0xffffffffu, got)) {
-      ok = false;
-      if (more) {  // let the copies already issued land before the warp leaves
-        nt_wait(bars + (buf ^ 1), (phase >> (buf ^ 1)) & 1u);
-        phase ^= 1u << (buf ^ 1);
-      }
-      break;
-    }
-#pragma unroll
-    for (int s2 = 0; s2 < PPH; ++s2) {
-      if (last[s2] >= 0) {
-        const float* hb = wbase + buf * Sh::kBuf + half * Sh::kHalf + s2 * 2 * kNtRegion;
-        if constexpr (PAIR) nt_fma2_chunk<MR, MC>(hb + mr * MR * kc[s2], hb + kNtRegion + mc * MC * kc[s2], kc[s2], p);
-        else nt_fma_chunk<MR, MC>(hb + mr * MR * kc[s2], hb + kNtRegion + mc * MC * kc[s2], kc[s2], p);
-        if (last[s2] && ++folded == kNtFold) {
+      if (last >= 0) {
+        const float* hb = wbase + buf * kNtBuf + half * kNtHalf;
+        nt_fma_chunk<MR, MC, CONST>(hb + mr * MR * kc, hb + kNtRegion + mc * MC * kc, kc, p);
+        if (last && ++folded == kNtFold) {
           folded = 0;
 #pragma unroll
-          for (int q = 0; q < NQ; ++q) {
-            float pt = PAIR ? p[q].x + p[q].y : p[q].x;
-            nt_fold(acc[q], pt);
-            p[q] = make_float2(pt, 0.0f);
-          }
+          for (int q = 0; q < NQ; ++q) nt_fold(acc[q], p[q]);
         }
       }
+      __syncwarp();
+      if (!more) break;
+      kc = half ? n1.kc : n0.kc;
+      last = half ? n1.last : n0.last;
+      buf ^= 1;
     }
-    __syncwarp();
-    if (!more) break;
-#pragma unroll
-    for (int s2 = 0; s2 < PPH; ++s2) {
-      kc[s2] = nkc[s2];
-      last[s2] = nlast[s2];
-    }
-    buf ^= 1;
   }
   // ---- combine the halves and write the tile -------------------------------------------
   float* cb = a.C + a.c_voff[k];
 #pragma unroll
   for (int q = 0; q < NQ; ++q) {
-    const float pq = PAIR ? p[q].x + p[q].y : p[q].x;
     const float oa = __shfl_xor_sync(0xffffffffu, acc[q], 16);
-    const float op = __shfl_xor_sync(0xffffffffu, pq, 16);
+    const float op = __shfl_xor_sync(0xffffffffu, p[q], 16);
     float s = acc[q];
     float e = oa;
     nt_fold(s, e);  // s = acc0 + acc1, e = its rounding error
     const int i = q / MC, j = q - i * MC;
     const int r = mr * MR + i, c = mc * MC + j;
     if (half == 0 && r < th && c < tw)
-      cb[(int64_t)(tile.r0 + r) * nj + tile.c0 + c] = ok ? s + (e + (pq + op)) : __int_as_float(0x7fc00000);
+      cb[(int64_t)(tile.r0 + r) * nj + tile.c0 + c] = ok ? s + (e + (p[q] + op)) : __int_as_float(0x7fc00000);
   }
   return ok;
 }
 
-template <bool PAIR, int PPH>
-__global__ void __launch_bounds__(kNtWarps * 32, PPH == 1 ? 4 : 2) mul_f32_nt_kernel(NtArgs a) {
-  using Sh = NtShape<PPH>;
-  extern __shared__ __align__(128) float nsm[];  // [warp][buffer][Sh::kBuf]
+template <bool CONST>
+__global__ void __launch_bounds__(kNtWarps * 32, 4) mul_f32_nt_kernel(NtArgs a) {
+  extern __shared__ __align__(128) float nsm[];  // [warp][buffer][kNtBuf]
   __shared__ __align__(8) uint64_t bars[kNtWarps][2];
   __shared__ __align__(16) NtEntry sent[kNtWarps][kNtEnt];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  float* wbase = nsm + (size_t)w * 2 * Sh::kBuf;  // the warp's two stage buffers
+  float* wbase = nsm + (size_t)w * 2 * kNtBuf;  // the warp's two stage buffers
   if (lane == 0) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(nt_smem(&bars[w][0])));
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(nt_smem(&bars[w][1])));
@@ -453,7 +406,7 @@ __global__ void __launch_bounds__(kNtWarps * 32, PPH == 1 ? 4 : 2) mul_f32_nt_ke
     uint64_t* bw = bars[w];
     NtEntry* en = sent[w];
 #define SF_NT_CASE(R, Cc) \
-  case (R - 1) * 5 + (Cc - 1): ok = nt_tile<R, Cc, PAIR, PPH>(a, tile, k, nu, nup, ni, nj, wb, bw, en, phase, lane); break;
+  case (R - 1) * 5 + (Cc - 1): ok = nt_tile<R, Cc, CONST>(a, tile, k, nu, nup, ni, nj, wb, bw, en, phase, lane); break;
     switch ((mr - 1) * 5 + (mc - 1)) {
       SF_NT_CASE(1, 1) SF_NT_CASE(1, 2) SF_NT_CASE(1, 3) SF_NT_CASE(1, 4) SF_NT_CASE(1, 5)
       SF_NT_CASE(2, 1) SF_NT_CASE(2, 2) SF_NT_CASE(2, 3) SF_NT_CASE(2, 4) SF_NT_CASE(2, 5)
@@ -611,7 +564,7 @@ bool nt_usable(const MulDesc& d, const void* X, const void* Y) {
   return true;
 }
 
-s_status launch_nt(const MulDesc& d, const void* X, const void* Y, void* C, cudaStream_t st, int form) {
+s_status launch_nt(const MulDesc& d, const void* X, const void* Y, void* C, cudaStream_t st, bool const_pitch) {
   if (d.ntiles == 0) return S_OK;
   s_status s = take_timeout(d);
   if (s) return s;
@@ -648,20 +601,14 @@ s_status launch_nt(const MulDesc& d, const void* X, const void* Y, void* C, cuda
   a.err = d.err;
   a.C = (float*)C;
   SF_CUDA(cudaMemsetAsync(d.counter, 0, sizeof(unsigned int), st));
-  // form: 1 one FMA per product, 2 packed FMAs; 3 and 4 the same with two pieces per half-warp
-  // and stage (half the warps per SM, half the per-stage bookkeeping per piece)
-  void (*kern)(NtArgs) = form == 2   ? mul_f32_nt_kernel<true, 1>
-                         : form == 3 ? mul_f32_nt_kernel<false, 2>
-                         : form == 4 ? mul_f32_nt_kernel<true, 2>
-                                     : mul_f32_nt_kernel<false, 1>;
-  const size_t smem = form >= 3 ? NtShape<2>::kSmem : NtShape<1>::kSmem;
-  SF_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  void (*kern)(NtArgs) = const_pitch ? mul_f32_nt_kernel<true> : mul_f32_nt_kernel<false>;
+  SF_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kNtSmem));
   int per_sm = 0;
-  SF_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kNtWarps * 32, smem));
+  SF_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kNtWarps * 32, kNtSmem));
   if (per_sm < 1) per_sm = 1;
   const int64_t want = (d.ntiles + kNtWarps - 1) / kNtWarps;
   const int grid = (int)std::min<int64_t>(want, (int64_t)sm_count() * per_sm);
-  kern<<<grid, kNtWarps * 32, smem, st>>>(a);
+  kern<<<grid, kNtWarps * 32, kNtSmem, st>>>(a);
   SF_CUDA(cudaGetLastError());
   return S_OK;
 }
