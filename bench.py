@@ -736,6 +736,8 @@ def main():
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
     achieved = flops / (statistics.mean(launch_ms) * 1e-3) / 1e12
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    probe = {"fp32_tflops": sf.peak_fma("fp32") / 1e12, "fp64_tflops": sf.peak_fma("fp64") / 1e12,
+             "how": "s_peak_fma: independent FMA chains on every lane, CUDA events"}
     if args.product == "fp32":
         fp32_peak = sms * 128 * 2 * sm_max * 1e6 / 1e12      # TFLOP/s from unit counts and clock
         nt = tuple(shape["micro"]) == (0, 0)
@@ -746,7 +748,8 @@ def main():
                           "split-K half-warps)" if nt else
                           "sf::mul_f32_kernel<tile %d, micro %dx%d, transposed A>" % (shape["tile"], *shape["micro"]),
                 "peak_source": "%d SMs (device attribute) x 128 FP32 lanes x 2 flop x %g MHz sm_max (derived)"
-                               % (sms, sm_max)}
+                               % (sms, sm_max),
+                "frac_of_probe": achieved / probe["fp32_tflops"], "probe": probe}
         launches = 1
     else:
         # tensor-core forms: useful flops against the dense peak of the operand type (bf16

@@ -288,6 +288,11 @@ s_status s_quad_form(s_pattern p, const double* X, const double* z, double* out,
 s_status s_quad_form_grad(s_pattern p, const double* z, double* dX, void* stream);
 
 /* ---- diagnostics ------------------------------------------------------------------------ */
+/* Measured multiply-add rate of this device in flop/s (2 per fused multiply-add), for the
+ * roofline denominators of the float (S_FP32) and double (S_FP64) product kernels:
+ * independent FMA chains on every lane of a grid of 8 CTAs of 256 threads per SM, the second of
+ * two launches timed with CUDA events on `stream`.  Synchronises the stream. */
+s_status s_peak_fma(s_prec prec, double* flops_per_s, void* stream);
 const char* s_last_error(void);
 /* Library version string. */
 const char* s_version(void);

@@ -66,6 +66,7 @@ def _load():
         "s_funm_sqrt_backward_prec": (i32, [vp, i32, i32, dbl, vp, vp, vp, vp]),
         "s_quad_form": (i32, [vp, vp, vp, P(dbl), vp]),
         "s_quad_form_grad": (i32, [vp, vp, vp, vp]),
+        "s_peak_fma": (i32, [i32, P(dbl), vp]),
         "s_last_error": (ctypes.c_char_p, []),
         "s_version": (ctypes.c_char_p, []),
     }
@@ -338,6 +339,13 @@ def funm(pattern, fn, A, F, steps=0, taylor_degree=0, prec="fp64", scale=0.0, sq
                  _ptr(checkpoints), int(refine))
     check(lib.s_funm(pattern.h, code, _ptr(A), _ptr(F), ctypes.byref(o), _stream(stream)))
     return float(res.value) if residual else None
+
+
+def peak_fma(prec="fp32", stream=None):
+    """Measured multiply-add rate of the device in flop/s (s_peak_fma)."""
+    v = ctypes.c_double()
+    check(lib.s_peak_fma(PREC[prec], ctypes.byref(v), _stream(stream)))
+    return float(v.value)
 
 
 def version():
