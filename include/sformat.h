@@ -231,7 +231,8 @@ s_status s_norm_est_noalloc(s_pattern p, const double* A, int iters, double* lam
 typedef struct {
   int steps;          /* Newton-Schulz steps (S_SQRT); 0 = 25                              */
   int taylor_degree;  /* Taylor degree (S_EXP, S_EXP_NEG); 0 = 8                            */
-  s_prec prec;        /* arithmetic of the products: S_FP64, S_FP64_DF or S_FP32            */
+  s_prec prec;        /* arithmetic of the products: S_FP64, S_FP64_DF, S_FP32, or a split
+                         tensor-core form S_TF32X3 / S_BF16X3 (float iterates as for S_FP32) */
   double scale;       /* S_SQRT: c with Y_0 = A/c (0 = 1.01 * norm estimate);
                          S_EXP*: lambda used for the squaring count (0 = norm estimate)     */
   int squarings;      /* S_EXP*: -1 = from lambda, else forced count                        */
@@ -251,8 +252,8 @@ typedef struct {
  *              grew by more than 1.5x on two consecutive steps while above 1e-3 of ||T_0 - I||_F.
  *   S_EXP, S_EXP_NEG   exp(+-A) by the power series of Sec. 4.4 truncated at the Taylor
  *              degree, Horner's rule on X = +-A/2^s, then s masked squarings,
- *              s = max(0, ceil(log2(lambda/0.5))).  With prec S_FP32 the Horner products
- *              run in float and the squarings in double.
+ *              s = max(0, ceil(log2(lambda/0.5))).  With prec S_FP32 (or a split tensor-core
+ *              form) the Horner products run in that arithmetic and the squarings in double.
  * With prec S_FP32, S_SQRT autotunes the float product kernel's shape on A first
  * (s_plan_autotune).  With prec S_FP64_DF the iterates are double and the products run in
  * double-float arithmetic.

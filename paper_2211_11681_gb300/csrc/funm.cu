@@ -157,10 +157,11 @@ extern "C" s_status s_funm(s_pattern p, s_fn fn, const double* A, double* F, con
   s_funm_opts o = {};
   if (opts) o = *opts;
   const s_prec prec = o.prec;
-  if (prec != S_FP64 && prec != S_FP32 && prec != S_FP64_DF)
-    return set_error(S_ERR_ARG, "s_funm: prec must be S_FP64, S_FP64_DF or S_FP32");
+  if (prec != S_FP64 && prec != S_FP32 && prec != S_FP64_DF && prec != S_TF32X3 && prec != S_BF16X3)
+    return set_error(S_ERR_ARG, "s_funm: prec must be S_FP64, S_FP64_DF, S_FP32, S_TF32X3 or S_BF16X3");
   // iterates are double for S_FP64 and S_FP64_DF (products in double-float), float for S_FP32
-  const s_prec aprec = prec == S_FP32 ? S_FP32 : S_FP64;
+  // and for the split tensor-core forms (S_TF32X3, S_BF16X3: float in, float out)
+  const s_prec aprec = (prec == S_FP64 || prec == S_FP64_DF) ? S_FP64 : S_FP32;
   const size_t w = aprec == S_FP64 ? sizeof(double) : sizeof(float);
   const int64_t nnz = p->d.nnz;
   s_plan plan = nullptr;

@@ -15,8 +15,8 @@
 // hi*hi + hi*lo + lo*hi are exact in the MMA; the dropped lo*lo and the rounding of lo are each
 // below 2^-22 |x y|, with random signs.  The tensor core's fp32 accumulation drops low bits
 // with a bias, so each stage starts a fresh accumulator (at most 9 MMAs deep) and the stage
-// sums are added over lambda in registers with round-to-nearest; independent accumulators also
-// let the MMAs of consecutive stages overlap.
+// sums are added over lambda in registers by error-free two-sums (compensated summation);
+// independent accumulators also let the MMAs of consecutive stages overlap.
 //
 // Staging: operands are K-major in the tensor core's no-swizzle canonical layout (8-row x
 // 16-byte core matrices; K-adjacent core matrices 128 bytes apart, 8-row groups kTcSBO bytes
@@ -297,7 +297,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) mul_tf32x3_kernel(TcArgs a) {
   int64_t g = 0;   // stages this CTA has issued
   int64_t gd = 0;  // stages whose accumulators have been added
   const int q = warp & 3, h = warp >> 2;  // this warp's TMEM lanes 32q .. and columns 16h ..
-  float acc[16];
+  float acc[16], cmp[16];  // stage sums, compensated: acc + cmp (error-free two-sums)
 
   for (;;) {
     if (tid == 0) {
@@ -329,8 +329,9 @@ __global__ void __launch_bounds__(kTcThreads, 1) mul_tf32x3_kernel(TcArgs a) {
     const int th = s_th, mused = s_mused;
     const int64_t e0 = s_e0, ne = s_ne;
 #pragma unroll
-    for (int u = 0; u < 16; ++u) acc[u] = 0.0f;
-    // stage k has finished: add its accumulator (rows 32q + lane, columns 16h ..) to acc
+    for (int u = 0; u < 16; ++u) acc[u] = cmp[u] = 0.0f;
+    // stage k has finished: add its accumulator (rows 32q + lane, columns 16h ..) to acc, the
+    // rounding error of every addition kept in cmp
     auto drain = [&](int64_t k) {
       const int b = (int)(k % kTcS);
       tc_wait(&mbar[b], (uint32_t)((k / kTcS) & 1), &s_abort, a.err);
@@ -345,7 +346,13 @@ __global__ void __launch_bounds__(kTcThreads, 1) mul_tf32x3_kernel(TcArgs a) {
             : "r"(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(b * kTcN + 16 * h)));
         asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
 #pragma unroll
-        for (int u = 0; u < 16; ++u) acc[u] += __uint_as_float(v[u]);
+        for (int u = 0; u < 16; ++u) {
+          const float x = __uint_as_float(v[u]);
+          const float sm = acc[u] + x;
+          const float bp = sm - acc[u];
+          cmp[u] += (acc[u] - (sm - bp)) + (x - bp);
+          acc[u] = sm;
+        }
       }
       asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
     };
@@ -470,7 +477,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) mul_tf32x3_kernel(TcArgs a) {
 #pragma unroll
         for (int u = 0; u < 16; ++u) {
           const int n = 16 * h + u;
-          if (n < th) cp[n * nj] = bad ? __int_as_float(0x7fc00000) : acc[u];
+          if (n < th) cp[n * nj] = bad ? __int_as_float(0x7fc00000) : acc[u] + cmp[u];
         }
       }
     }

@@ -109,3 +109,32 @@ def test_divergence_is_reported(sphere):
     assert e.value.status == sf.S_ERR_NOT_CONVERGED
     # the library stays usable afterwards
     sf.funm(P, "sqrt", dev(A.val), F, steps=25)
+
+
+@pytest.mark.parametrize("prec", ["tf32x3", "bf16x3"])
+def test_tensor_core_forms_in_the_drivers(sphere, prec):
+    # the split tensor-core products (float iterates) drive the same iterations: the square
+    # root with two double residual corrections lands near the oracle's corrected double
+    # result (the tensor-core products are about ten times less accurate than the compensated
+    # float ones, so the start is ~2e-6 away; the two corrections contract by ~0.1 and ~0.25:
+    # ~5e-8, bound 3e-7), and the exponential (tensor-core Horner products, double squarings)
+    # within the float-class bound of the other mixed form
+    from paper_2211_11681_gb300 import sformat as sf
+    c, levels = sphere
+    A = c.A
+    P = pattern_of(A, levels)
+    F = dev(np.zeros(len(A.val)))
+    if prec == "bf16x3" and np.any(A.bsize % 2):
+        # split-bfloat16 staging needs even block sizes: refused with S_ERR_ARG, no device work
+        with pytest.raises(sf.SFormatError) as e:
+            sf.funm(P, "sqrt", dev(A.val), F, steps=25, prec=prec, refine=2)
+        assert e.value.status == sf.S_ERR_ARG
+        return
+    X = ofunm.sqrtm_ns(A, steps=25, nthreads=8, refine=2)
+    sf.funm(P, "sqrt", dev(A.val), F, steps=25, prec=prec, refine=2)
+    assert rel_frob(host(F), X.val) <= 3e-7
+    A12 = A.like(A.val * 12.0)
+    E = ofunm.expm_taylor(A12, sign=-1.0, nthreads=8)
+    G = dev(np.zeros(len(A.val)))
+    sf.funm(P, "exp_neg", dev(A12.val), G, prec=prec)
+    assert rel_frob(host(G), E.val) <= 1e-5
