@@ -67,8 +67,8 @@ typedef enum {
  *   S_TF32X3   float in, float out; each operand split as hi + lo, both rounded to TF32
  *              (10 fraction bits), the three products hi*hi + hi*lo + lo*hi on the tcgen05
  *              tensor cores, each lambda slice (at most 24 wide) accumulated in fp32 in
- *              tensor memory and the slices summed in fp32 registers.  Blocks may be at
- *              most 96 wide.  Inputs must be finite. */
+ *              tensor memory and the slices summed in fp32 registers by error-free two-sums
+ *              (compensated).  Blocks may be at most 96 wide.  Inputs must be finite. */
 typedef enum { S_FP64 = 0, S_FP32 = 1, S_BF16X3 = 2, S_FP64_DF = 3, S_TF32X3 = 4 } s_prec;
 
 typedef enum { S_SQRT = 0, S_EXP = 1, S_EXP_NEG = 2 } s_fn;

@@ -9,9 +9,9 @@ Tolerances: FP64 within 1e-12 relative Frobenius over the sampled blocks, mixed
 (compensated float) within 1e-6, split-bfloat16 tensor-core products within 5e-6: the
 tensor cores' float accumulation over the 18 k8 steps of a lambda slice loses about 2^-23
 per step (measured 2.2e-6 over the whole product), above the 1e-6 the compensated float
-kernel reaches.  Split-TF32 (tcgen05) within 5e-6 as well: each stage's accumulator is at most
-nine MMAs deep, but the sums over hundreds of lambda stages are plain float additions
-(measured 2.5e-6 over the whole product)."""
+kernel reaches.  Split-TF32 (tcgen05) within 1e-6: each stage's accumulator is at most nine
+MMAs deep and the sums over the lambda stages are compensated (measured 3.8e-7 over the whole
+product)."""
 import os
 
 import numpy as np
@@ -72,4 +72,4 @@ def test_fullsize_sampled_parity(c2):
     assert np.linalg.norm(c64[idx] - want) <= 1e-12 * n
     assert np.linalg.norm(c32[idx] - want) <= 1e-6 * n
     assert np.linalg.norm(cb[idx] - want) <= 5e-6 * n
-    assert np.linalg.norm(ct[idx] - want) <= 5e-6 * n
+    assert np.linalg.norm(ct[idx] - want) <= 1e-6 * n
