@@ -84,6 +84,25 @@ def build_input(w, n):
     return b, pat, vals, {"host_s": round(t1 - t0, 2), "values_s": round(t2 - t1, 2)}
 
 
+def compression_error(b, pat, vals, w, n, seed=23):
+    """||T K T^T y - K^eta y|| / ||T K T^T y|| for y = T x, x a seeded Gaussian vector: the
+    uncompressed kernel matrix applied on the device (every entry evaluated), the samplet
+    transform on the host, the compressed matrix by s_spmm."""
+    import torch
+    import workloads as W
+    from paper_2211_11681_gb300 import sformat as sf
+    x = W.random_vector(n, seed)
+    t0 = time.time()
+    tkx = b.transform(b.kernel_matvec(w.nu, w.ell, 1.0 / n, w.nugget, x))
+    tx = torch.from_numpy(b.transform(x)).cuda().reshape(1, n)
+    ky = torch.empty_like(tx)
+    sf.spmm(pat, vals, tx, ky)
+    ref = torch.from_numpy(tkx).cuda()
+    e = float((ref - ky[0]).norm() / ref.norm())
+    return {"value": e, "seconds": round(time.time() - t0, 2),
+            "how": "||T K x - K^eta T x|| / ||T K x||, x ~ N(0, I) (seed %d), K x with every entry evaluated" % seed}
+
+
 def algorithmic_bytes(pat, width):
     # each operand read once, C written once, plus the pattern's index arrays
     bo, rp, ci = pat.arrays()
@@ -732,6 +751,7 @@ def main():
            "pipelined": "two buffers; uploads and downloads on their own streams overlap neighbouring products"}
     del Ah, Ch, Ad, Cd
 
+    comp_err = compression_error(b, pat, vals, w, n) if not args.no_fp64 else None
     peaks = measured_peaks()
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
     achieved = flops / (statistics.mean(launch_ms) * 1e-3) / 1e12
@@ -770,7 +790,7 @@ def main():
         "warmup": args.warmup, "ms_per_step": round(ms, 3), "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": dtype, "data": "synthetic",
         "config": dict(workload_config(w, n, pat, triples, flops), parallelism="replicas" if world > 1 else "1 GPU",
-                       arithmetic=args.product, prep_seconds=prep),
+                       arithmetic=args.product, prep_seconds=prep, compression_error_estimate=comp_err),
         "hbm_gbs_algorithmic": qbytes / (ms * 1e-3) / 1e9,
         "fp64": fp64,
         "roofline": roof,

@@ -74,6 +74,14 @@ s_status s_build_values(s_build b, double nu, double ell, double kscale, double 
  * no nugget, no threshold, written to the caller's device buffer `out`
  * (s_pattern_nnz(on) doubles).  Same device algorithm as s_build_values. */
 s_status s_build_values_dell(s_build b, double nu, double ell, double kscale, s_pattern on, double* out);
+/* y = (kscale K + nugget I) v for host vectors v, y of length n in original point order, with
+ * every entry of the uncompressed kernel matrix K evaluated on the device (float evaluations,
+ * double row sums; O(n^2), about a second at n = 2^20).  With the samplet transform
+ * (s_build_transform) and the compressed values it estimates the compression error
+ * ||T K T^T w - K^eta w|| / ||T K T^T w|| for w = T v without forming T K T^T (Thm.
+ * (S-compression) bounds that error).  Synchronous. */
+s_status s_build_kernel_matvec(s_build b, double nu, double ell, double kscale, double nugget, const double* v,
+                               double* y);
 /* Copies the held values into the caller's device buffer `dst` (s_pattern_nnz doubles)
  * on `stream`, waits for the copy, and releases the builder's copy. */
 s_status s_build_take_values(s_build b, double* dst, void* stream);

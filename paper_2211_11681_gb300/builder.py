@@ -22,6 +22,7 @@ for _name, (_res, _args) in {
     "s_build_take_values": (_i32, [_vp, _vp, _vp]),
     "s_build_values_dell": (_i32, [_vp, _dbl, _dbl, _dbl, _vp, _vp]),
     "s_build_transform": (_i32, [_vp, _P(_dbl), _P(_dbl)]),
+    "s_build_kernel_matvec": (_i32, [_vp, _dbl, _dbl, _dbl, _dbl, _P(_dbl), _P(_dbl)]),
 }.items():
     _f = getattr(lib, _name)
     _f.restype = _res
@@ -110,6 +111,15 @@ class Builder:
         _sf.check(lib.s_build_values_dell(self.h, float(nu), float(ell), float(kscale), pattern.h,
                                           _vp(out.data_ptr())))
         return out[:pattern.nnz]
+
+    def kernel_matvec(self, nu, ell, kscale, nugget, v):
+        """(kscale K + nugget I) v with the uncompressed kernel matrix (host vectors, original
+        point order)."""
+        v = np.ascontiguousarray(v, dtype=np.float64)
+        out = np.zeros(self.n)
+        _sf.check(lib.s_build_kernel_matvec(self.h, float(nu), float(ell), float(kscale), float(nugget),
+                                            v.ctypes.data_as(_P(_dbl)), out.ctypes.data_as(_P(_dbl))))
+        return out
 
     def transform(self, v):
         """T v (samplet coordinates) of a host vector in original point order."""

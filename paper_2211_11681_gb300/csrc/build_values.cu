@@ -642,6 +642,69 @@ extern "C" s_status s_build_values(s_build b, double nu, double ell, double ksca
   return values_impl(b, nu, ell, kscale, nugget, tau, false, nullptr, nullptr, pattern);
 }
 
+// y = (kscale K + nugget I) v with every kernel entry evaluated (no compression): one thread
+// per row, columns streamed through shared memory 1024 at a time; each tile's terms summed in
+// float, the tiles in double.
+constexpr int kMvTile = 1024;
+__global__ void __launch_bounds__(256) kmatvec_kernel(const float* __restrict__ x, int64_t n, int p, float inv_ell,
+                                                      float scale, const float* __restrict__ v, double* __restrict__ y) {
+  __shared__ float sx[kMvTile][3];
+  __shared__ float sv[kMvTile];
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const bool row = i < n;
+  const float xi0 = row ? x[i * 3] : 0.f, xi1 = row ? x[i * 3 + 1] : 0.f, xi2 = row ? x[i * 3 + 2] : 0.f;
+  double acc = 0.0;
+  for (int64_t j0 = 0; j0 < n; j0 += kMvTile) {
+    const int cnt = (int)(n - j0 < kMvTile ? n - j0 : (int64_t)kMvTile);
+    __syncthreads();
+    for (int t = threadIdx.x; t < cnt; t += blockDim.x) {
+      sx[t][0] = x[(j0 + t) * 3];
+      sx[t][1] = x[(j0 + t) * 3 + 1];
+      sx[t][2] = x[(j0 + t) * 3 + 2];
+      sv[t] = v[j0 + t];
+    }
+    __syncthreads();
+    float part = 0.f;
+    for (int t = 0; t < cnt; ++t) {
+      const float d0 = xi0 - sx[t][0], d1 = xi1 - sx[t][1], d2 = xi2 - sx[t][2];
+      const float r = sqrtf(fmaf(d0, d0, fmaf(d1, d1, d2 * d2)));
+      part = fmaf(matern(r, p, inv_ell, scale), sv[t], part);
+    }
+    acc += (double)part;
+  }
+  if (row) y[i] = acc;
+}
+
+extern "C" s_status s_build_kernel_matvec(s_build b, double nu, double ell, double kscale, double nugget,
+                                          const double* v, double* y) {
+  if (!b || !v || !y) return set_error(S_ERR_ARG, "s_build_kernel_matvec: NULL argument");
+  int p;
+  if (std::fabs(nu - 0.5) < 1e-12) p = 0;
+  else if (std::fabs(nu - 1.5) < 1e-12) p = 1;
+  else if (std::fabs(nu - 2.5) < 1e-12) p = 2;
+  else return set_error(S_ERR_ARG, "s_build_kernel_matvec: nu must be 0.5, 1.5 or 2.5");
+  if (!(ell > 0.0)) return set_error(S_ERR_ARG, "s_build_kernel_matvec: ell must be positive");
+  const int64_t n = b->n;
+  std::vector<float> xf((size_t)n * 3, 0.0f), vf(n);
+  for (int64_t i = 0; i < n; ++i) {
+    for (int a = 0; a < b->d; ++a) xf[i * 3 + a] = (float)b->points[i * b->d + a];
+    vf[i] = (float)v[i];
+  }
+  Frees fr;
+  s_status st;
+  float *dx, *dv;
+  double* dy;
+  if ((st = upload(&dx, xf)) || (st = upload(&dv, vf)) || (st = dmalloc(&dy, (size_t)n))) return st;
+  fr.add(dx);
+  fr.add(dv);
+  fr.add(dy);
+  kmatvec_kernel<<<(unsigned)((n + 255) / 256), 256>>>(dx, n, p, (float)(1.0 / ell), (float)kscale, dv, dy);
+  SF_CUDA(cudaGetLastError());
+  SF_CUDA(cudaMemcpy(y, dy, sizeof(double) * n, cudaMemcpyDeviceToHost));
+  for (int64_t i = 0; i < n; ++i) y[i] += nugget * v[i];
+  return S_OK;
+}
+
 extern "C" s_status s_build_values_dell(s_build b, double nu, double ell, double kscale, s_pattern on, double* out) {
   if (!b || !on || (!out && on->d.nnz > 0)) return set_error(S_ERR_ARG, "s_build_values_dell: NULL argument");
   return values_impl(b, nu, ell, kscale, 0.0, 0.0, true, on, out, nullptr);

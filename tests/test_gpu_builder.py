@@ -64,3 +64,30 @@ def test_builder_threshold_is_symmetric_and_close_to_oracle():
     for (i, j) in got ^ want:
         m = K[boff[i]:boff[i + 1], boff[j]:boff[j + 1]].max()
         assert i != j and abs(m - w.tau) <= band, (i, j, m)
+
+
+def test_compression_error_estimate_matches_dense():
+    # ||T K T^T y - K^eta y|| / ||T K T^T y|| with y = T x: the device's uncompressed matvec,
+    # the fast transform and s_spmm against the oracle's dense T K T^T and dense K^eta on the
+    # same points (T agrees to 1e-12; the device evaluates K in float, ~1e-7 of ||K x||)
+    import torch
+    from paper_2211_11681_gb300 import sformat as sf
+    from paper_2211_11681_gb300.builder import Builder
+    w = W.WORKLOADS["matern12_3d_1m"]
+    n = 4096
+    x = W.points(w, n)
+    c = compress_kernel(x, w.nu, w.ell, w.q, w.leaf, w.eta, w.tau, 1.0 / n, w.nugget)
+    v = W.random_vector(n, 23)
+    y = c.basis.T @ v
+    want = np.linalg.norm(c.Khat @ y - c.A.to_dense() @ y) / np.linalg.norm(c.Khat @ y)
+    b = Builder(x, w.leaf, w.q, w.eta)
+    pat, vals = b.values(w.nu, w.ell, 1.0 / n, w.nugget, w.tau)
+    kx = b.kernel_matvec(w.nu, w.ell, 1.0 / n, w.nugget, v)
+    dense_kx = (c.basis.T.T @ c.Khat @ c.basis.T) @ v          # T^T (T K T^T) T v = K v
+    assert np.linalg.norm(kx - dense_kx) <= 1e-6 * np.linalg.norm(dense_kx)
+    tkx = b.transform(kx)
+    ty = torch.from_numpy(b.transform(v)).cuda().reshape(1, n)
+    ky = torch.empty_like(ty)
+    sf.spmm(pat, vals, ty, ky)
+    got = np.linalg.norm(tkx - ky[0].cpu().numpy()) / np.linalg.norm(tkx)
+    assert got == pytest.approx(want, rel=0.05, abs=1e-7)
