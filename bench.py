@@ -606,7 +606,7 @@ def main():
         return
 
     from paper_2211_11681_gb300 import sformat as sf
-    b, pat, vals, prep = build_input(w, n)
+    bld, pat, vals, prep = build_input(w, n)
     t0 = time.time()
     plan32 = sf.Plan(pat, pat, pat, args.product)
     plan32.set_symmetric_a(True)      # A = T K T^T (+ mu I) is symmetric
@@ -751,7 +751,7 @@ def main():
            "pipelined": "two buffers; uploads and downloads on their own streams overlap neighbouring products"}
     del Ah, Ch, Ad, Cd
 
-    comp_err = compression_error(b, pat, vals, w, n) if not args.no_fp64 else None
+    comp_err = compression_error(bld, pat, vals, w, n) if not args.no_fp64 else None
     peaks = measured_peaks()
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
     achieved = flops / (statistics.mean(launch_ms) * 1e-3) / 1e12
