@@ -48,6 +48,7 @@ def parse():
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--batch", type=int, default=256, help="matrices of the batched workload")
+    ap.add_argument("--batch-log2", default="10,16", help="batched workload: N log-uniform in [2^a, 2^b]")
     ap.add_argument("--precisions", default="fp64,fp64_df,mixed", help="drivers mode: arithmetic forms to run")
     ap.add_argument("--tau", type=float, default=None, help="override the workload's threshold")
     ap.add_argument("--variant", type=int, default=-1,
@@ -263,7 +264,8 @@ def run_batch(args, rank, world):
     import workloads as W
     from paper_2211_11681_gb300 import sformat as sf
     from paper_2211_11681_gb300.builder import Builder
-    ws = W.batch_workloads(count=args.batch)
+    lo, hi = (int(v) for v in args.batch_log2.split(","))
+    ws = W.batch_workloads(count=args.batch, nmin_log2=lo, nmax_log2=hi)
     t0 = time.time()
     pats, parts = [], []
     t_host = t_dev = 0.0
@@ -335,7 +337,7 @@ def run_batch(args, rank, world):
     torch.cuda.synchronize()
     ms_loop = e0.elapsed_time(e1) / args.steps
     n = len(ws)
-    line = {"metric": "batched masked S-products/s (%d matrices, N log-uniform 2^10..2^16)" % n,
+    line = {"metric": "batched masked S-products/s (%d matrices, N log-uniform 2^%d..2^%d)" % (n, lo, hi),
             "value": n / (ms * 1e-3), "unit": "products/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": round(ms, 3), "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
