@@ -116,17 +116,19 @@ s_status s_plan_create(s_pattern A, s_pattern B, s_pattern C, s_prec prec, s_pla
 s_status s_plan_destroy(s_plan plan);
 /* Exact triple count and useful flop count of the plan's product. */
 s_status s_plan_stats(s_plan plan, int64_t* triples, double* flops);
-/* Autotuner of S_FP32 and S_FP64_DF plans: times the kernel variants of the plan's
+/* Autotuner of S_FP64, S_FP32 and S_FP64_DF plans: times the kernel variants of the plan's
  * arithmetic (output tile edge, the micro-tile of one lane, for float also the lambda extent
  * of a stage) on the given operands and keeps the fastest for this plan's forward product.
+ * (S_FP64 plans have tile edges 20 and 10; a plan whose output blocks have a
+ * root-mean-square edge of at most 12 starts with 10, the others with 20.)
  * Each variant runs one timed warm-up launch; one more than twice as slow as the best so far
  * stops there, the others are timed over three more launches.  Float tile and row-panel
  * shapes narrower than the root-mean-square block edge of S_C are skipped.  C is
- * overwritten.  *chosen (optional) receives the variant index.  S_FP64, S_BF16X3 and
- * S_TF32X3 plans have one shape (no-op).  Synchronises the stream. */
+ * overwritten.  *chosen (optional) receives the variant index.  S_BF16X3 and S_TF32X3
+ * plans have one shape (no-op).  Synchronises the stream. */
 s_status s_plan_autotune(s_plan plan, const void* A, const void* B, void* C, void* stream, int* chosen);
 /* Selects kernel variant `variant` (0 .. s_plan_num_variants_of(plan)-1) for the plan's
- * forward product by hand (S_FP32 and S_FP64_DF plans). */
+ * forward product by hand (S_FP64, S_FP32 and S_FP64_DF plans). */
 s_status s_plan_set_variant(s_plan plan, int variant);
 /* Number of float variants; number of variants of a plan's arithmetic (1 when fixed). */
 int s_plan_num_variants(void);

@@ -106,11 +106,13 @@ __global__ void tile_fill_kernel(const int64_t* first, const int32_t* bsize, con
 constexpr int kWarps = 8;
 template <typename T>
 constexpr bool kCompensated = sizeof(T) == 4;
-constexpr int kPer = (kTile * kTile + 31) / 32;  // accumulators per lane
-
-template <typename T, bool TX, bool TY>
+// Double product: tile edge TT (20, or 10 for patterns of blocks at most about 10 wide),
+// every lane holding (TT^2 + 31) / 32 entries of the tile.
+template <typename T, int TT, bool TX, bool TY>
 __global__ void __launch_bounds__(kWarps * 32) mul_kernel(MulArgs a, const T* __restrict__ X,
                                                           const T* __restrict__ Y, T* __restrict__ C) {
+  constexpr int kTile = TT;
+  constexpr int kPer = (TT * TT + 31) / 32;  // accumulators per lane
   __shared__ T sX[kWarps][kTile * kTile];
   __shared__ T sY[kWarps][kTile * kTile];
   const int lane = threadIdx.x & 31;
@@ -1256,6 +1258,14 @@ constexpr int kF32Fallback = 2;  // tile kernel of the K-major variants' tile li
 
 static int num_sms() { return sm_count(); }
 
+// Tile edges of the double product's variants; plans of narrow blocks start with the 10-wide one.
+constexpr int kF64Edges[] = {20, 10};
+constexpr int kNumF64Variants = 2;
+static int f64_default_variant(const s_pattern_t* C) {
+  const double rms = std::sqrt((double)C->d.nnz / (double)std::max<int64_t>(C->d.nblocks, 1));
+  return rms <= 12.0 ? 1 : 0;
+}
+
 static Side side_of(const s_pattern_t* p, bool row_side, bool trans) {
   // row_side: the list indexed by the output row (X side); otherwise by the output column.
   const DevPattern& d = p->d;
@@ -1353,7 +1363,12 @@ s_status build_desc(const s_pattern_t* X, bool tx, const s_pattern_t* Y, bool ty
     }
   }
   if (e != cudaSuccess) st = cuda_error(e, "s_plan_create(symbolic)");
-  if (!st) st = build_tiles(&d, kF32Variants[0].tt);
+  if (!st && prec == S_FP64) {
+    d.variant = f64_default_variant(C);
+    st = build_tiles(&d, kF64Edges[d.variant]);
+  } else if (!st) {
+    st = build_tiles(&d, kF32Variants[0].tt);
+  }
   if (!st && prec == S_BF16X3) {
     // three bfloat16 planes per operand; every block size must be even (4-byte copies)
     for (const s_pattern_t* q : {X, Y, C})
@@ -1507,9 +1522,14 @@ static s_status launch_typed(const MulDesc& d, const void* X, const void* Y, voi
     dsmem = f32_smem(v);
     SF_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dsmem));
   } else {
-    if (d.edge != kTile) return set_error(S_ERR_ARG, "internal: double kernel needs 20-wide tiles");
-    kern = d.x.trans ? (d.y.trans ? mul_kernel<T, true, true> : mul_kernel<T, true, false>)
-                     : (d.y.trans ? mul_kernel<T, false, true> : mul_kernel<T, false, false>);
+    const int tt = kF64Edges[d.variant < kNumF64Variants ? d.variant : 0];
+    if (d.edge != tt) return set_error(S_ERR_ARG, "internal: tile list does not match the double variant");
+    if (tt == 10)
+      kern = d.x.trans ? (d.y.trans ? mul_kernel<T, 10, true, true> : mul_kernel<T, 10, true, false>)
+                       : (d.y.trans ? mul_kernel<T, 10, false, true> : mul_kernel<T, 10, false, false>);
+    else
+      kern = d.x.trans ? (d.y.trans ? mul_kernel<T, 20, true, true> : mul_kernel<T, 20, true, false>)
+                       : (d.y.trans ? mul_kernel<T, 20, false, true> : mul_kernel<T, 20, false, false>);
     warps = kWarps;
   }
   SF_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, warps * 32, dsmem));
@@ -1732,13 +1752,13 @@ extern "C" s_status s_mul_masked_adjoint(s_plan p, const void* dC, const void* A
 
 extern "C" s_status s_plan_autotune(s_plan p, const void* A, const void* B, void* C, void* stream, int* chosen) {
   if (!p || !A || !B || !C) return set_error(S_ERR_ARG, "s_plan_autotune: NULL argument");
-  if (p->prec != S_FP32 && p->prec != S_FP64_DF) {
+  if (p->prec != S_FP32 && p->prec != S_FP64_DF && p->prec != S_FP64) {
     if (chosen) *chosen = 0;
-    return S_OK;  // one kernel shape for the double and split-bfloat16 paths
+    return S_OK;  // one kernel shape for the split tensor-core paths
   }
-  const bool df = p->prec == S_FP64_DF;
-  const int nvar = df ? kNumDfVariants : kNumF32Variants;
-  auto edge_of = [&](int v) { return df ? kDfVariants[v].tt : kF32Variants[v].tt; };
+  const bool df = p->prec == S_FP64_DF, f64 = p->prec == S_FP64;
+  const int nvar = df ? kNumDfVariants : (f64 ? kNumF64Variants : kNumF32Variants);
+  auto edge_of = [&](int v) { return df ? kDfVariants[v].tt : (f64 ? kF64Edges[v] : kF32Variants[v].tt); };
   cudaStream_t st = (cudaStream_t)stream;
   cudaEvent_t e0, e1;
   SF_CUDA(cudaEventCreate(&e0));
@@ -1751,10 +1771,12 @@ extern "C" s_status s_plan_autotune(s_plan p, const void* A, const void* B, void
   const s_pattern_t* pc = p->fwd.pc;
   const double rms_edge = std::sqrt((double)pc->d.nnz / (double)std::max<int64_t>(pc->d.nblocks, 1));
   for (int v = 0; v < nvar && !s; ++v) {
-    const bool panel = !df && kF32Variants[v].panel;
+    const bool fl = !df && !f64;
+    const bool panel = fl && kF32Variants[v].panel;
     if (panel && rms_edge > kF32Variants[v].tt) continue;
     // tile shapes narrower than 20 only where the blocks are no wider than their tiles
-    if (!df && !panel && !kF32Variants[v].nt && kF32Variants[v].tt < 20 && rms_edge > kF32Variants[v].tt) continue;
+    if (fl && !panel && !kF32Variants[v].nt && kF32Variants[v].tt < 20 && rms_edge > kF32Variants[v].tt) continue;
+    if (f64 && kF64Edges[v] < 20 && rms_edge > 12.0) continue;
     if ((s = build_tiles(&p->fwd, edge_of(v)))) break;
     if (panel && (s = build_panels(&p->fwd, kF32Variants[v].tt, kF32Variants[v].panel))) break;
     p->fwd.variant = v;
@@ -1792,7 +1814,7 @@ extern "C" s_status s_plan_autotune(s_plan p, const void* A, const void* B, void
   cudaEventDestroy(e1);
   if (s) return s;
   if ((s = build_tiles(&p->fwd, edge_of(bestv)))) return s;
-  if (!df && kF32Variants[bestv].panel &&
+  if (!df && !f64 && kF32Variants[bestv].panel &&
       (s = build_panels(&p->fwd, kF32Variants[bestv].tt, kF32Variants[bestv].panel)))
     return s;
   p->fwd.variant = bestv;
@@ -1812,6 +1834,14 @@ extern "C" s_status s_plan_variant(s_plan p, int variant, int* tile, int* micro_
     if (stage_k) *stage_k = kDfVariants[variant].tt;
     return S_OK;
   }
+  if (p->prec == S_FP64) {
+    if (variant >= kNumF64Variants) return set_error(S_ERR_ARG, "s_plan_variant: no such variant");
+    if (tile) *tile = kF64Edges[variant];
+    if (micro_rows) *micro_rows = 1;
+    if (micro_cols) *micro_cols = 1;
+    if (stage_k) *stage_k = kF64Edges[variant];
+    return S_OK;
+  }
   if (p->prec == S_TF32X3) {
     if (tile) *tile = kTcN;
     if (micro_rows) *micro_rows = kTcM;
@@ -1829,13 +1859,14 @@ extern "C" s_status s_plan_variant(s_plan p, int variant, int* tile, int* micro_
 
 extern "C" s_status s_plan_set_variant(s_plan p, int variant) {
   if (!p) return set_error(S_ERR_ARG, "s_plan_set_variant: NULL plan");
-  if (p->prec != S_FP32 && p->prec != S_FP64_DF)
-    return set_error(S_ERR_ARG, "s_plan_set_variant: only float and double-float plans have variants");
-  const bool df = p->prec == S_FP64_DF;
-  if (variant < 0 || variant >= (df ? kNumDfVariants : kNumF32Variants))
+  if (p->prec != S_FP32 && p->prec != S_FP64_DF && p->prec != S_FP64)
+    return set_error(S_ERR_ARG, "s_plan_set_variant: only double, float and double-float plans have variants");
+  const bool df = p->prec == S_FP64_DF, f64 = p->prec == S_FP64;
+  if (variant < 0 || variant >= (df ? kNumDfVariants : (f64 ? kNumF64Variants : kNumF32Variants)))
     return set_error(S_ERR_ARG, "s_plan_set_variant: no such variant");
-  s_status s = build_tiles(&p->fwd, df ? kDfVariants[variant].tt : kF32Variants[variant].tt);
-  if (!s && !df && kF32Variants[variant].panel)
+  s_status s = build_tiles(&p->fwd, df ? kDfVariants[variant].tt
+                                       : (f64 ? kF64Edges[variant] : kF32Variants[variant].tt));
+  if (!s && !df && !f64 && kF32Variants[variant].panel)
     s = build_panels(&p->fwd, kF32Variants[variant].tt, kF32Variants[variant].panel);
   if (s) return s;
   p->fwd.variant = variant;
@@ -1845,7 +1876,10 @@ extern "C" s_status s_plan_set_variant(s_plan p, int variant) {
 extern "C" int s_plan_num_variants(void) { return kNumF32Variants; }
 extern "C" int s_plan_num_variants_of(s_plan p) {
   if (!p) return 0;
-  return p->prec == S_FP32 ? kNumF32Variants : (p->prec == S_FP64_DF ? kNumDfVariants : 1);
+  return p->prec == S_FP32     ? kNumF32Variants
+         : p->prec == S_FP64_DF ? kNumDfVariants
+         : p->prec == S_FP64    ? kNumF64Variants
+                                : 1;
 }
 
 extern "C" s_status s_plan_set_symmetric_a(s_plan p, int symmetric) {

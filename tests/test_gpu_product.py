@@ -46,6 +46,7 @@ def test_c1_fp64_parity(sf, c1):
     plan = sf.Plan(P, P, P, "fp64")
     t, f = plan.stats()
     assert (t, f) == oprod.mul_count(A, A, A)
+    assert plan.variant()["tile"] == 10            # 6- and 10-wide blocks: the 10-wide tiles
     dA = dev(A.val)
     dC = dev(np.full(len(A.val), np.nan))
     plan.mul(dA, dA, dC)
@@ -79,10 +80,12 @@ def test_general_patterns_and_ragged_tiles(sf, seed):
     pa, pb, pc = pattern_of(A), pattern_of(B), pattern_of(Cp)
     plan = sf.Plan(pa, pb, pc, "fp64")
     assert plan.stats() == oprod.mul_count(A, B, Cp)
-    out = dev(np.full(len(Cp.val), np.nan))
-    plan.mul(dev(A.val), dev(B.val), out)
     want = oprod.mul_masked(A, B, Cp).val
-    assert rel_frob(host(out), want) <= 1e-12
+    for v in range(plan.num_variants()):       # tile edges 20 and 10
+        plan.set_variant(v)
+        out = dev(np.full(len(Cp.val), np.nan))
+        plan.mul(dev(A.val), dev(B.val), out)
+        assert rel_frob(host(out), want) <= 1e-12, v
     # FP32 arithmetic on the same values
     p32 = sf.Plan(pa, pb, pc, "fp32")
     o32 = dev(np.zeros(len(Cp.val)), "float32")
