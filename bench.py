@@ -734,10 +734,12 @@ def main():
     def pipeline(steps):
         """`steps` end-to-end steps; returns the milliseconds from the first upload to the last
         download."""
-        ev = lambda: torch.cuda.Event()
+        ev = lambda: torch.cuda.Event(enable_timing=True)
         up = [ev() for _ in range(steps)]
         done = [ev() for _ in range(steps)]
         down = [ev() for _ in range(steps)]
+        h2d0 = [ev() for _ in range(steps)]
+        d2h0 = [ev() for _ in range(steps)]
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
@@ -747,6 +749,7 @@ def main():
             with torch.cuda.stream(s_h2d):
                 if i >= 2:
                     s_h2d.wait_event(done[i - 2])        # buffer b no longer read by step i-2
+                h2d0[i].record(s_h2d)
                 Ad[b].copy_(Ah, non_blocking=True)
                 up[i].record(s_h2d)
             stream.wait_event(up[i])
@@ -756,12 +759,17 @@ def main():
             done[i].record(stream)
             with torch.cuda.stream(s_d2h):
                 s_d2h.wait_event(done[i])
+                d2h0[i].record(s_d2h)
                 Ch[b].copy_(Cd[b], non_blocking=True)
                 down[i].record(s_d2h)
         stream.wait_event(down[steps - 1])
         e1.record(stream)
         torch.cuda.synchronize()
+        copy_ms[0] = statistics.median(h2d0[i].elapsed_time(up[i]) for i in range(steps))
+        copy_ms[1] = statistics.median(d2h0[i].elapsed_time(down[i]) for i in range(steps))
         return e0.elapsed_time(e1)
+
+    copy_ms = [0.0, 0.0]
 
     # warm-up steps: the first DMA through freshly pinned host pages runs at a small fraction of
     # the warm rate (measured 10 GB/s cold against 211 GB/s warm), a one-time cost of the buffers
@@ -771,7 +779,8 @@ def main():
            "h2d_bytes_per_step": int(Ah.numel() * 4), "d2h_bytes_per_step": int(Ch[0].numel() * 4),
            "ms_per_step": round(e2e_ms, 3), "steps": e2e_steps,
            "pipelined": "two buffers; uploads and downloads on their own streams overlap neighbouring products",
-           "warmup_steps": max(2, args.warmup)}
+           "warmup_steps": max(2, args.warmup),
+           "copy_ms_median": {"h2d": round(copy_ms[0], 2), "d2h": round(copy_ms[1], 2)}}
     del Ah, Ch, Ad, Cd
 
     peaks = measured_peaks()
