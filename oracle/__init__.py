@@ -23,6 +23,9 @@ Modules and the passage of the paper each one follows:
             (the power series of Sec. 4.4 with squaring added).
   adjoint   reverse mode of the masked product and of the Newton-Schulz iteration.
   estimators  the error estimator e_F of the multiplication benchmark (Sec. 5.1).
+  selinv    selected inversion P_S((A + sigma I)^{-1}) and the block elimination game for
+            the pattern of the factor (Sec. 4.2, Eq. (blockInv)).
+  contour   A^{-1/2} by the contour-integral quadrature, Eq. (ContInt) (Sec. 4.4).
 
 Every function with no independent pin says "parity unpinned" in its docstring.  At the
 time of writing every function is pinned by a test under ``tests/test_oracle_*.py``.
