@@ -57,8 +57,11 @@ def parse():
     ap.add_argument("--tau", type=float, default=None, help="override the workload's threshold")
     ap.add_argument("--variant", type=int, default=-1,
                     help="float kernel variant to time (default: the autotuner's choice)")
-    ap.add_argument("--sizes", default="5000,10000,50000,100000,250000,500000,1000000",
-                    help="paper_mult_2d/3d: the N of the sweep")
+    ap.add_argument("--sizes", default=None,
+                    help="paper_mult_2d/3d (default 5000,...,1000000) and selinv_2d (default its N): the N of the "
+                         "sweep")
+    ap.add_argument("--mus", default="1e-2,1e-4,1e-6", help="selinv workload: ridge parameters")
+    ap.add_argument("--nodes", type=int, default=7, help="contour workload: quadrature nodes of Eq. (ContInt)")
     ap.add_argument("--product", choices=["fp32", "tf32x3", "bf16x3"], default="fp32",
                     help="arithmetic of the timed product: compensated float (default) or a split "
                          "tensor-core form")
@@ -370,7 +373,8 @@ def run_paper_mult(args, rank, world):
     from paper_2211_11681_gb300 import sformat as sf
     from paper_2211_11681_gb300.builder import Builder
     w = W.WORKLOADS[args.workload]
-    ns = [args.n] if args.n else [int(v) for v in args.sizes.split(",")]
+    sizes = args.sizes or ",".join(str(v) for v in W.PAPER_MULT_NS)
+    ns = [args.n] if args.n else [int(v) for v in sizes.split(",")]
     stream = torch.cuda.current_stream()
     rows = []
 
@@ -437,6 +441,165 @@ def run_paper_mult(args, rank, world):
                        "estimator": "e_F(M) = ||M X||_F/||X||_F, X in R^{N x 10} uniform [0,1]"},
             "points": rows,
             "paper_context": "Sec. 5.1 plots e_F between 1e-8 and 2e-6 for N = 5e3..1e6 (point values not in the source)"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+def run_selinv(args, rank, world):
+    """Selected inversion on the compression pattern (Sec. 4.2, Eq. (blockInv); the inversion
+    experiment of Sec. 5.2): (K + mu I)^{-1} on the a-posteriori pattern of K, the compressed
+    exponential kernel exp(-r)/N (q+1 = 4 vanishing moments, eta = 1.25, tau = 1e-5/N) on
+    uniform points in [0,1]^2, for ridge parameters mu = 1e-2, 1e-4, 1e-6.  Timed: one block
+    LDL^T factorization and one selected inversion (FP64, CUDA events), and the paper's error
+    e_F(Z (K + mu I) - I) with X in R^{N x 10} uniform.  One JSON line per N, then a summary."""
+    import torch
+    import workloads as W
+    from paper_2211_11681_gb300 import selinv as si
+    from paper_2211_11681_gb300 import sformat as sf
+    from paper_2211_11681_gb300.builder import Builder
+    w = W.WORKLOADS[args.workload]
+    ns = [args.n] if args.n else ([int(v) for v in args.sizes.split(",")] if args.sizes else [w.n])
+    mus = [float(v) for v in args.mus.split(",")]
+    stream = torch.cuda.current_stream()
+    peak64 = sf.peak_fma("fp64")
+    rows = []
+    for n in ns:
+        x = W.points(w, n)
+        b = Builder(x, w.leaf, w.q, w.eta)
+        pat, K = b.values(w.nu, w.ell, 1.0 / n, 0.0, W.tau_of(w, n))
+        del b
+        t0 = time.time()
+        inv = si.SelInv(pat)
+        sym_s = time.time() - t0
+        st = inv.stats()
+        flops = st["flops_factor"] + st["flops_invert"]
+        g = torch.Generator(device="cuda")
+        g.manual_seed(99)
+        X = torch.rand((10, n), dtype=torch.float64, device="cuda", generator=g)
+        T1, T2 = torch.empty_like(X), torch.empty_like(X)
+        Z = torch.empty_like(K)
+        pts = []
+        for mu in mus:
+            inv.factor(K, mu)
+            inv.invert(Z)
+            inv.status()
+            e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+            reps = max(1, args.steps)
+            fac = ivt = 0.0
+            for _ in range(reps):
+                e[0].record(stream)
+                inv.factor(K, mu)
+                e[1].record(stream)
+                inv.invert(Z)
+                e[2].record(stream)
+                torch.cuda.synchronize()
+                fac += e[0].elapsed_time(e[1])
+                ivt += e[1].elapsed_time(e[2])
+            inv.status()
+            fac, ivt = fac / reps, ivt / reps
+            sf.spmm(pat, K, X, T1)
+            T1 += mu * X                                  # (K + mu I) X
+            sf.spmm(pat, Z, T1, T2)                       # Z (K + mu I) X
+            ef = float((T2 - X).norm() / X.norm())
+            pts.append({"mu": mu, "factor_ms": round(fac, 3), "invert_ms": round(ivt, 3),
+                        "gflops": flops / ((fac + ivt) * 1e6), "frac_fp64_peak": flops / ((fac + ivt) * 1e-3) / peak64,
+                        "e_F": ef})
+        row = {"n": n, "nnz": pat.nnz, "blocks": pat.nblocks, "l_blocks": st["l_blocks"],
+               "l_entries": st["l_entries"], "levels": st["levels"], "flops_factor": st["flops_factor"],
+               "flops_invert": st["flops_invert"], "symbolic_s": round(sym_s, 3), "points": pts}
+        rows.append(row)
+        if rank == 0:
+            print(json.dumps({"selinv_point": row}), flush=True)
+        del inv, K, Z, X, T1, T2, pat
+        torch.cuda.empty_cache()
+    last = rows[-1]
+    best = min(last["points"], key=lambda p: p["factor_ms"] + p["invert_ms"])
+    line = {"metric": "selected inversion (K + mu I)^{-1} on the a-posteriori pattern (Sec. 4.2, 5.2): ms per "
+                      "factorization + inversion",
+            "value": round(best["factor_ms"] + best["invert_ms"], 3), "unit": "ms (FP64, largest N)",
+            "higher_is_better": False, "n_gpus": world, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": w.name, "d": w.d, "kernel": "exp(-r)/N (Matern-1/2, ell=1)", "q": w.q,
+                       "eta": w.eta, "tau": "1e-5/N", "leaf": w.leaf, "mu": mus,
+                       "estimator": "e_F(Z (K + mu I) - I), X in R^{N x 10} uniform [0,1]"},
+            "roofline": {"bound": "fp64", "achieved": best["gflops"] / 1e3, "peak": peak64 / 1e12, "unit": "TFLOP/s",
+                         "frac": best["frac_fp64_peak"],
+                         "peak_source": "s_peak_fma FP64 (FMA chains on every lane), measured in this run"},
+            "points": rows,
+            "paper_context": "Sec. 5.2 (Pardiso, 16 Xeon cores): e_F falls with growing mu; times plotted, "
+                             "point values not in the source"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+def run_contour(args, rank, world):
+    """Eq. (ContInt), the matrix-function experiment of Sec. 5.3: A = K + mu I with K the
+    compressed exp(-2r)/N kernel matrix (q+1 = 4, eta = 1.25, tau = 1e-5/N) on points of a
+    closed surface (the unit sphere standing in for the 3D scan), mu = 1e-4, c_lo = mu,
+    c_hi = 1, n = 7 nodes: A^{-1/2} on S by seven shifted selected inversions, A^{1/2} =
+    P_S(A A^{-1/2}) by the masked product, and e_F(A^{1/2} A^{1/2} - A); the Newton-Schulz
+    square root on the same S beside it."""
+    import torch
+    import workloads as W
+    from paper_2211_11681_gb300 import selinv as si
+    from paper_2211_11681_gb300 import sformat as sf
+    from paper_2211_11681_gb300.builder import Builder
+    w = W.WORKLOADS[args.workload]
+    n = args.n or w.n
+    mu, nodes = w.nugget, args.nodes
+    stream = torch.cuda.current_stream()
+    x = W.points(w, n)
+    b = Builder(x, w.leaf, w.q, w.eta)
+    pat, A = b.values(w.nu, w.ell, 1.0 / n, mu, W.tau_of(w, n))
+    del b
+    t0 = time.time()
+    inv = si.SelInv(pat)
+    sym_s = time.time() - t0
+    st = inv.stats()
+    Zi = torch.empty_like(A)
+    inv.invsqrt(A, mu, 1.0, nodes, Zi)
+    e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+    p64 = sf.Plan(pat, pat, pat, "fp64")
+    R = torch.empty_like(A)
+    e0.record(stream)
+    inv.invsqrt(A, mu, 1.0, nodes, Zi)
+    e1.record(stream)
+    p64.mul(A, Zi, R)
+    e2.record(stream)
+    torch.cuda.synchronize()
+    ms_inv, ms_mul = e0.elapsed_time(e1), e1.elapsed_time(e2)
+    g = torch.Generator(device="cuda")
+    g.manual_seed(99)
+    X = torch.rand((10, n), dtype=torch.float64, device="cuda", generator=g)
+    T1, T2, T3 = (torch.empty_like(X) for _ in range(3))
+    sf.spmm(pat, R, X, T1)
+    sf.spmm(pat, R, T1, T2)
+    sf.spmm(pat, A, X, T3)
+    ef = float((T2 - T3).norm() / X.norm())
+    F = torch.empty_like(A)
+    t1 = time.time()
+    sf.funm(pat, "sqrt", A, F, steps=25)
+    torch.cuda.synchronize()
+    ns_s = time.time() - t1
+    sf.spmm(pat, F, X, T1)
+    sf.spmm(pat, F, T1, T2)
+    ef_ns = float((T2 - T3).norm() / X.norm())
+    flops = nodes * (st["flops_factor"] + st["flops_invert"])
+    peak64 = sf.peak_fma("fp64")
+    line = {"metric": "A^{1/2} by the contour integral Eq. (ContInt) with selected inversion: ms",
+            "value": round(ms_inv + ms_mul, 3), "unit": "ms (FP64)", "higher_is_better": False, "n_gpus": world,
+            "dtype": "f64", "data": "synthetic",
+            "config": {"workload": w.name, "n": n, "kernel": "exp(-2r)/N (Matern-1/2, ell=0.5)", "q": w.q,
+                       "eta": w.eta, "tau": "1e-5/N", "mu": mu, "c_lo": mu, "c_hi": 1.0, "nodes": nodes,
+                       "points": "unit sphere (stand-in for the 3D scan)"},
+            "invsqrt_ms": round(ms_inv, 3), "sqrt_product_ms": round(ms_mul, 3),
+            "selinv": {"nnz": pat.nnz, "l_blocks": st["l_blocks"], "l_entries": st["l_entries"],
+                       "levels": st["levels"], "symbolic_s": round(sym_s, 3)},
+            "roofline": {"bound": "fp64", "achieved": flops / (ms_inv * 1e-3) / 1e12, "peak": peak64 / 1e12,
+                         "unit": "TFLOP/s", "frac": flops / (ms_inv * 1e-3) / peak64,
+                         "peak_source": "s_peak_fma FP64, measured in this run"},
+            "e_F_sqrt_sqrt_minus_A": ef, "newton_schulz": {"steps": 25, "wall_s": round(ns_s, 3), "e_F": ef_ns},
+            "rel_frob_contour_vs_ns": float((R - F).norm() / F.norm()),
+            "paper_context": "Table (Sec. 5.3), 3D scan, K = 7: e_F 1.43e-3 (N = 5000) .. 2.82e-4 (N = 100000)"}
     if rank == 0:
         print(json.dumps(line), flush=True)
 
@@ -592,6 +755,12 @@ def main():
         return
     if args.workload.startswith("paper_mult"):
         run_paper_mult(args, rank, world)
+        if dist is not None:
+            dist.barrier()
+            dist.destroy_process_group()
+        return
+    if args.workload.startswith("selinv") or args.workload.startswith("contour"):
+        (run_selinv if args.workload.startswith("selinv") else run_contour)(args, rank, world)
         if dist is not None:
             dist.barrier()
             dist.destroy_process_group()

@@ -47,7 +47,9 @@ typedef enum {
   S_ERR_NOMEM = -4,         /* device or host allocation failed                       */
   S_ERR_CUDA = -5,          /* a CUDA call failed; see s_last_error()                 */
   S_ERR_NOT_CONVERGED = -6, /* Newton-Schulz iteration diverged (see s_funm)          */
-  S_ERR_TIMEOUT = -7        /* a bounded device-side wait ran out                     */
+  S_ERR_TIMEOUT = -7,       /* a bounded device-side wait ran out                     */
+  S_ERR_NOT_SPD = -8        /* a factorization met a pivot block that is not positive
+                               definite (sselinv.h)                                    */
 } s_status;
 
 /* Arithmetic of a product.

@@ -35,7 +35,8 @@ def sources():
 def _compile(src, verbose):
     obj = os.path.join(OBJ_DIR, os.path.basename(src) + ".o")
     deps = [src] + [os.path.join(CSRC, h) for h in os.listdir(CSRC) if h.endswith((".cuh", ".h"))]
-    deps.append(os.path.join(ROOT, "include", "sformat.h"))
+    inc = os.path.join(ROOT, "include")
+    deps += [os.path.join(inc, h) for h in os.listdir(inc) if h.endswith(".h")]
     if os.path.exists(obj) and os.path.getmtime(obj) >= max(os.path.getmtime(d) for d in deps):
         return obj
     cmd = [nvcc()] + ARCH + NVFLAGS + ["-c", src, "-o", obj]

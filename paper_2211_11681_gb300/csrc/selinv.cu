@@ -1,0 +1,835 @@
+// Selected inversion on the compression pattern (Sec. 4.2 "Sparse selected inversion",
+// Eq. (blockInv)) and the contour-integral inverse square root (Sec. 4.4, Eq. (ContInt)),
+// in FP64.
+//
+// Supernodes are the clusters: every non-empty cluster is one block column of the factor,
+// its samplets a dense block.  The host picks a minimum-degree elimination order of the
+// block graph of S, plays the elimination game to get the pattern of L (position space,
+// i >= k), and lists the blocks of every level of the elimination tree.  Blocks whose
+// columns sit on one level are independent, so each level is one launch:
+//
+//   factor, levels from the leaves up (A + sigma I = L D L^T, W = L D kept beside L):
+//     update  W(i,k) = A(i,k) + sigma [i = k] - sum_{j < k} W(i,j) L(k,j)^T over the j in
+//             both row i and row k of L (one warp per output block and 512-entry tile);
+//     pivot   D(k,k) = W(k,k) inverted by Gauss-Jordan in shared memory (positive definite:
+//             no pivoting; a pivot that is not positive is recorded), then
+//             L(i,k) = W(i,k) D(k,k)^{-1} for the blocks of column k (a CTA per supernode
+//             and slice of its column), D^{-1} stored in L's diagonal block;
+//   inversion, levels from the root down (Takahashi-type recurrences from Eq. (blockInv)):
+//     off     Z(i,k) = - sum_{j in struct(k)} Z(i,j) L(j,k), Z(i,j) read from block
+//             (max, min) of Z, transposed when i < j (one warp per output block and tile);
+//     diag    Z(k,k) = D(k,k)^{-1} - sum_{j in struct(k)} Z(j,k)^T L(j,k) (a CTA per
+//             supernode);
+//   scatter   out = alpha P_S(Z) + beta out, blocks of S read from Z or its transpose.
+//
+// Every entry an update reads was written by an earlier launch (descendants sit on lower
+// levels, ancestors on higher ones), so the kernels need no synchronisation beyond stream
+// order and no waits.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "common.cuh"
+#include "sselinv.h"
+
+namespace sf {
+namespace {
+
+constexpr int kSiMaxB = 64;               // widest block
+constexpr int kSiEnt = 16;                // output entries per lane
+constexpr int kSiTileEnt = 32 * kSiEnt;   // entries of one work item
+constexpr int kSiWarps = 4;               // warps per CTA of the block kernels
+constexpr int kSiThreads = 128;           // threads of the pivot and diagonal kernels
+constexpr int kSiSlice = 8;               // column blocks per pivot CTA
+constexpr int kSiMaxClusters = 32768;     // non-empty clusters of the host bitset analysis
+
+struct SiItem {
+  int32_t blk;  // CSC block of L
+  int32_t col;  // its column position
+  int32_t e0;   // first entry of the tile
+};
+
+struct SiDev {
+  const int32_t* bs;      // block size per position
+  const int64_t* colptr;  // CSC of L: column k holds blocks colptr[k] .. colptr[k+1]-1,
+  const int32_t* colrow;  //   the diagonal first, then the rows of struct(k) ascending
+  const int64_t* loff;    // entry offset of each CSC block (rows x cols, row-major)
+  const int64_t* rowptr;  // CSR of L: row i holds columns ascending, the diagonal last
+  const int32_t* rowcol;
+  const int32_t* rowblk;  // CSC block of each CSR entry
+  const int64_t* aoff;    // per CSC block: entry offset of the S block with its rows and
+                          // columns (-1: not in S)
+  double* W;              // L D (D in the diagonal blocks)
+  double* L;              // L (D^{-1} in the diagonal blocks)
+  double* Z;              // the inverse on the pattern of L
+  unsigned int* flag;     // mapped host word: 1 = a pivot block was not positive definite
+};
+
+__device__ __forceinline__ int64_t si_lower_bound(const int32_t* a, int64_t lo, int64_t hi, int32_t v) {
+  while (lo < hi) {
+    const int64_t mid = (lo + hi) >> 1;
+    if (__ldg(a + mid) < v) lo = mid + 1;
+    else hi = mid;
+  }
+  return lo;
+}
+
+// factor update: W(i,k) = A(i,k) + sigma [i = k] - sum_j W(i,j) L(k,j)^T
+__global__ void __launch_bounds__(kSiWarps * 32) si_update_kernel(SiDev s, const SiItem* __restrict__ items,
+                                                                   int64_t nitems, const double* __restrict__ A,
+                                                                   double sigma) {
+  const int lane = threadIdx.x & 31;
+  const int64_t wid = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  if (wid >= nitems) return;
+  const SiItem it = items[wid];
+  const int i = s.colrow[it.blk], k = it.col;
+  const int bi = s.bs[i], bk = s.bs[k];
+  const int ne = bi * bk;
+  const int64_t ao = s.aoff[it.blk];
+  double acc[kSiEnt];
+  int rr[kSiEnt], cc[kSiEnt];
+#pragma unroll
+  for (int m = 0; m < kSiEnt; ++m) {
+    const int e = it.e0 + lane + 32 * m;
+    rr[m] = e < ne ? e / bk : -1;
+    cc[m] = e < ne ? e - rr[m] * bk : 0;
+    double v = 0.0;
+    if (e < ne) {
+      if (ao >= 0) v = A[ao + e];
+      if (i == k && rr[m] == cc[m]) v += sigma;
+    }
+    acc[m] = v;
+  }
+  // j over row k of L below the diagonal, matched in row i
+  const int64_t ri1 = s.rowptr[i + 1];
+  const int64_t rk0 = s.rowptr[k], rk1 = s.rowptr[k + 1] - 1;
+  int64_t lo = s.rowptr[i];
+  for (int64_t base = rk0; base < rk1; base += 32) {
+    const int64_t q = base + lane;
+    const int32_t j = q < rk1 ? __ldg(s.rowcol + q) : INT32_MAX;
+    const int64_t a = si_lower_bound(s.rowcol, lo, ri1, j);
+    const bool hit = q < rk1 && a < ri1 && __ldg(s.rowcol + a) == j;
+    const int bij = hit ? __ldg(s.rowblk + a) : 0;
+    const int bkj = hit ? __ldg(s.rowblk + q) : 0;
+    unsigned int mask = __ballot_sync(0xffffffffu, hit);
+    lo = __shfl_sync(0xffffffffu, a, 31);
+    while (mask) {
+      const int src = __ffs(mask) - 1;
+      mask &= mask - 1u;
+      const int jj = __shfl_sync(0xffffffffu, j, src);
+      const int64_t wo = s.loff[__shfl_sync(0xffffffffu, bij, src)];
+      const int64_t lo2 = s.loff[__shfl_sync(0xffffffffu, bkj, src)];
+      const int bj = s.bs[jj];
+      const double* __restrict__ Wij = s.W + wo;   // bi x bj
+      const double* __restrict__ Lkj = s.L + lo2;  // bk x bj
+#pragma unroll
+      for (int m = 0; m < kSiEnt; ++m) {
+        if (rr[m] < 0) continue;
+        const double* wr = Wij + (int64_t)rr[m] * bj;
+        const double* lr = Lkj + (int64_t)cc[m] * bj;
+        double t = 0.0;
+        for (int u = 0; u < bj; ++u) t = fma(wr[u], lr[u], t);
+        acc[m] -= t;
+      }
+    }
+  }
+  double* out = s.W + s.loff[it.blk];
+#pragma unroll
+  for (int m = 0; m < kSiEnt; ++m)
+    if (rr[m] >= 0) out[it.e0 + lane + 32 * m] = acc[m];
+}
+
+// Gauss-Jordan inverse of the bk x bk block M (row-major, shared) without pivoting; returns
+// false (in every thread) if a pivot was not a positive finite number.
+__device__ bool si_gauss_jordan(double* M, int bk, double* prow, double* pcol) {
+  bool ok = true;
+  for (int p = 0; p < bk; ++p) {
+    const double piv = M[p * bk + p];
+    if (!(piv > 0.0) || !isfinite(piv)) ok = false;
+    const double inv = 1.0 / piv;
+    for (int t = threadIdx.x; t < bk; t += blockDim.x) {
+      prow[t] = t == p ? inv : M[p * bk + t] * inv;
+      pcol[t] = M[t * bk + p];
+    }
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < bk * bk; idx += blockDim.x) {
+      const int r = idx / bk, c = idx - r * bk;
+      if (r == p) M[idx] = prow[c];
+      else M[idx] = (c == p ? 0.0 : M[idx]) - pcol[r] * prow[c];
+    }
+    __syncthreads();
+  }
+  return ok;
+}
+
+// pivot: D(k,k)^{-1} and L(i,k) = W(i,k) D(k,k)^{-1}; CTA (x, y) serves supernode sn[x] and
+// the column blocks y*kSiSlice+1 .. of it; slice 0 stores D^{-1}.
+__global__ void __launch_bounds__(kSiThreads) si_pivot_kernel(SiDev s, const int32_t* __restrict__ sn) {
+  extern __shared__ double smem[];
+  __shared__ double prow[kSiMaxB], pcol[kSiMaxB];
+  const int k = sn[blockIdx.x];
+  const int bk = s.bs[k];
+  const int64_t c0 = s.colptr[k], c1 = s.colptr[k + 1];
+  const int64_t q0 = c0 + 1 + (int64_t)blockIdx.y * kSiSlice;
+  if (blockIdx.y > 0 && q0 >= c1) return;
+  double* M = smem;
+  const double* D = s.W + s.loff[c0];
+  for (int idx = threadIdx.x; idx < bk * bk; idx += blockDim.x) M[idx] = D[idx];
+  __syncthreads();
+  const bool ok = si_gauss_jordan(M, bk, prow, pcol);
+  if (blockIdx.y == 0) {
+    if (!ok && threadIdx.x == 0) {
+      *(volatile unsigned int*)s.flag = 1u;
+      __threadfence_system();
+    }
+    double* Dinv = s.L + s.loff[c0];
+    for (int idx = threadIdx.x; idx < bk * bk; idx += blockDim.x) Dinv[idx] = M[idx];
+  }
+  const int64_t q1 = min(c1, q0 + kSiSlice);
+  for (int64_t q = q0; q < q1; ++q) {
+    const int bi = s.bs[s.colrow[q]];
+    const double* Wq = s.W + s.loff[q];
+    double* Lq = s.L + s.loff[q];
+    for (int idx = threadIdx.x; idx < bi * bk; idx += blockDim.x) {
+      const int r = idx / bk, c = idx - r * bk;
+      const double* wr = Wq + (int64_t)r * bk;
+      double t = 0.0;
+      for (int u = 0; u < bk; ++u) t = fma(wr[u], M[u * bk + c], t);
+      Lq[idx] = t;
+    }
+  }
+}
+
+// inversion, off-diagonal blocks: Z(i,k) = - sum_{j in struct(k)} Z(i,j) L(j,k)
+__global__ void __launch_bounds__(kSiWarps * 32) si_offdiag_kernel(SiDev s, const SiItem* __restrict__ items,
+                                                                    int64_t nitems) {
+  const int lane = threadIdx.x & 31;
+  const int64_t wid = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  if (wid >= nitems) return;
+  const SiItem it = items[wid];
+  const int i = s.colrow[it.blk], k = it.col;
+  const int bi = s.bs[i], bk = s.bs[k];
+  const int ne = bi * bk;
+  double acc[kSiEnt];
+  int rr[kSiEnt], cc[kSiEnt];
+#pragma unroll
+  for (int m = 0; m < kSiEnt; ++m) {
+    const int e = it.e0 + lane + 32 * m;
+    rr[m] = e < ne ? e / bk : -1;
+    cc[m] = e < ne ? e - rr[m] * bk : 0;
+    acc[m] = 0.0;
+  }
+  const int64_t q0 = s.colptr[k] + 1, q1 = s.colptr[k + 1];
+  for (int64_t base = q0; base < q1; base += 32) {
+    const int64_t q = base + lane;
+    const bool valid = q < q1;
+    const int j = valid ? __ldg(s.colrow + q) : 0;
+    // block (max(i,j), min(i,j)) of Z: row max in the CSC column min
+    const int hi = max(i, j), lw = min(i, j);
+    int zb = -1;
+    if (valid) {
+      const int64_t a0 = s.colptr[lw], a1 = s.colptr[lw + 1];
+      const int64_t a = si_lower_bound(s.colrow, a0, a1, hi);
+      if (a < a1 && __ldg(s.colrow + a) == hi) zb = (int)a;
+    }
+    unsigned int mask = __ballot_sync(0xffffffffu, zb >= 0);
+    while (mask) {
+      const int src = __ffs(mask) - 1;
+      mask &= mask - 1u;
+      const int jj = __shfl_sync(0xffffffffu, j, src);
+      const int zz = __shfl_sync(0xffffffffu, zb, src);
+      const int64_t qq = base + src;
+      const int bj = s.bs[jj];
+      const bool tr = i < jj;                          // Z(i,j) = Z(j,i)^T
+      const double* __restrict__ Zp = s.Z + s.loff[zz];  // bi x bj, or bj x bi when tr
+      const double* __restrict__ Ljk = s.L + s.loff[qq]; // bj x bk
+#pragma unroll
+      for (int m = 0; m < kSiEnt; ++m) {
+        if (rr[m] < 0) continue;
+        double t = 0.0;
+        if (tr) {
+          for (int u = 0; u < bj; ++u) t = fma(Zp[(int64_t)u * bi + rr[m]], Ljk[(int64_t)u * bk + cc[m]], t);
+        } else {
+          const double* zr = Zp + (int64_t)rr[m] * bj;
+          for (int u = 0; u < bj; ++u) t = fma(zr[u], Ljk[(int64_t)u * bk + cc[m]], t);
+        }
+        acc[m] -= t;
+      }
+    }
+  }
+  double* out = s.Z + s.loff[it.blk];
+#pragma unroll
+  for (int m = 0; m < kSiEnt; ++m)
+    if (rr[m] >= 0) out[it.e0 + lane + 32 * m] = acc[m];
+}
+
+// inversion, diagonal blocks: Z(k,k) = D^{-1} - sum_{j in struct(k)} Z(j,k)^T L(j,k)
+__global__ void __launch_bounds__(kSiThreads) si_diag_kernel(SiDev s, const int32_t* __restrict__ sn) {
+  const int k = sn[blockIdx.x];
+  const int bk = s.bs[k];
+  const int64_t c0 = s.colptr[k], c1 = s.colptr[k + 1];
+  const double* Dinv = s.L + s.loff[c0];
+  double* Zkk = s.Z + s.loff[c0];
+  for (int idx = threadIdx.x; idx < bk * bk; idx += blockDim.x) {
+    const int r = idx / bk, c = idx - r * bk;
+    double t = 0.0;
+    for (int64_t q = c0 + 1; q < c1; ++q) {
+      const int bj = s.bs[s.colrow[q]];
+      const double* Zq = s.Z + s.loff[q];  // bj x bk
+      const double* Lq = s.L + s.loff[q];
+      for (int u = 0; u < bj; ++u) t = fma(Zq[(int64_t)u * bk + r], Lq[(int64_t)u * bk + c], t);
+    }
+    Zkk[idx] = Dinv[idx] - t;
+  }
+}
+
+// out = alpha P_S(Z) + beta out: one warp per block of S
+__global__ void si_scatter_kernel(int64_t nblocks, const int32_t* __restrict__ sbsize,
+                                  const int32_t* __restrict__ sbrow, const int32_t* __restrict__ scol,
+                                  const int64_t* __restrict__ svoff, const int32_t* __restrict__ s2l,
+                                  const int8_t* __restrict__ s2t, const int64_t* __restrict__ loff,
+                                  const double* __restrict__ Z, double alpha, double beta, double* __restrict__ out) {
+  const int lane = threadIdx.x & 31;
+  for (int64_t b = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; b < nblocks;
+       b += ((int64_t)gridDim.x * blockDim.x) >> 5) {
+    const int br = sbsize[sbrow[b]], bc = sbsize[scol[b]];
+    const int lb = s2l[b];
+    if (lb < 0) continue;  // an empty block
+    const bool tr = s2t[b] != 0;
+    const double* zb = Z + loff[lb];
+    double* o = out + svoff[b];
+    for (int e = lane; e < br * bc; e += 32) {
+      const int r = e / bc, c = e - r * bc;
+      const double z = tr ? zb[(int64_t)c * br + r] : zb[e];
+      o[e] = beta == 0.0 ? alpha * z : alpha * z + beta * o[e];
+    }
+  }
+}
+
+// ---- host: symbolic analysis ------------------------------------------------------------
+
+struct Symbolic {
+  int32_t m = 0;                         // non-empty clusters
+  std::vector<int32_t> perm;             // position -> cluster (non-empty first)
+  std::vector<int32_t> pos;              // cluster -> position (-1: empty cluster)
+  std::vector<std::vector<int32_t>> st;  // struct(p): positions below p in column p, ascending
+};
+
+// Symmetric, sorted, in-range pattern check; returns S_ERR_PATTERN on a violation.
+s_status check_symmetric(int32_t nc, const int64_t* rowptr, const int32_t* colidx) {
+  for (int32_t r = 0; r < nc; ++r) {
+    for (int64_t q = rowptr[r]; q < rowptr[r + 1]; ++q) {
+      const int32_t c = colidx[q];
+      if (c < 0 || c >= nc || (q > rowptr[r] && colidx[q - 1] >= c))
+        return set_error(S_ERR_PATTERN, "selected inversion: pattern rows must be sorted and in range");
+      const int32_t* b = colidx + rowptr[c];
+      const int32_t* e = colidx + rowptr[c + 1];
+      const int32_t* f = std::lower_bound(b, e, r);
+      if (f == e || *f != r) return set_error(S_ERR_PATTERN, "selected inversion: the pattern is not symmetric");
+    }
+  }
+  return S_OK;
+}
+
+// Minimum degree on the block graph (exact degrees, bitset rows), ties to the smaller id.
+s_status symbolic(int32_t nc, const int64_t* rowptr, const int32_t* colidx, const int32_t* bsize, Symbolic* out) {
+  s_status st = check_symmetric(nc, rowptr, colidx);
+  if (st) return st;
+  std::vector<int32_t> vid(nc, -1), cl;
+  for (int32_t c = 0; c < nc; ++c)
+    if (bsize[c] > 0) {
+      vid[c] = (int32_t)cl.size();
+      cl.push_back(c);
+    }
+  const int32_t m = (int32_t)cl.size();
+  if (m > kSiMaxClusters) return set_error(S_ERR_ARG, "selected inversion: more than 32768 non-empty clusters");
+  const int64_t W = (m + 63) / 64;
+  std::vector<uint64_t> adj((size_t)m * W, 0ull), alive((size_t)W, 0ull);
+  for (int32_t v = 0; v < m; ++v) alive[v >> 6] |= 1ull << (v & 63);
+  for (int32_t v = 0; v < m; ++v) {
+    const int32_t r = cl[v];
+    for (int64_t q = rowptr[r]; q < rowptr[r + 1]; ++q) {
+      const int32_t u = vid[colidx[q]];
+      if (u >= 0 && u != v) adj[(size_t)v * W + (u >> 6)] |= 1ull << (u & 63);
+    }
+  }
+  std::vector<int32_t> deg(m);
+  for (int32_t v = 0; v < m; ++v) {
+    int d = 0;
+    for (int64_t w = 0; w < W; ++w) d += __builtin_popcountll(adj[(size_t)v * W + w]);
+    deg[v] = d;
+  }
+  std::vector<uint8_t> done(m, 0);
+  std::vector<int32_t> order;
+  order.reserve(m);
+  std::vector<std::vector<int32_t>> nbv(m);
+  std::vector<int32_t> nb;
+  for (int32_t step = 0; step < m; ++step) {
+    int32_t v = -1;
+    for (int32_t u = 0; u < m; ++u)
+      if (!done[u] && (v < 0 || deg[u] < deg[v])) v = u;
+    done[v] = 1;
+    alive[v >> 6] &= ~(1ull << (v & 63));
+    order.push_back(v);
+    uint64_t* av = &adj[(size_t)v * W];
+    nb.clear();
+    for (int64_t w = 0; w < W; ++w) {
+      uint64_t x = av[w] & alive[w];
+      av[w] = x;
+      while (x) {
+        const int b = __builtin_ctzll(x);
+        x &= x - 1;
+        nb.push_back((int32_t)(w * 64 + b));
+      }
+    }
+    nbv[v] = nb;
+    for (int32_t u : nb) {
+      uint64_t* au = &adj[(size_t)u * W];
+      int d = 0;
+      for (int64_t w = 0; w < W; ++w) {
+        const uint64_t x = (au[w] | av[w]) & alive[w];
+        au[w] = x;
+        d += __builtin_popcountll(x);
+      }
+      au[u >> 6] &= ~(1ull << (u & 63));
+      deg[u] = d - 1;  // the union held u itself (u is a neighbour of v)
+    }
+  }
+  out->m = m;
+  out->perm.assign(nc, 0);
+  out->pos.assign(nc, -1);
+  std::vector<int32_t> vpos(m);
+  for (int32_t p = 0; p < m; ++p) {
+    vpos[order[p]] = p;
+    out->perm[p] = cl[order[p]];
+    out->pos[cl[order[p]]] = p;
+  }
+  int32_t p = m;
+  for (int32_t c = 0; c < nc; ++c)
+    if (bsize[c] <= 0) out->perm[p++] = c;
+  out->st.assign(m, {});
+  for (int32_t q = 0; q < m; ++q) {
+    const int32_t v = order[q];
+    std::vector<int32_t>& s = out->st[q];
+    s.reserve(nbv[v].size());
+    for (int32_t u : nbv[v]) s.push_back(vpos[u]);
+    std::sort(s.begin(), s.end());
+  }
+  return S_OK;
+}
+
+std::vector<int32_t> etree_levels(const Symbolic& sy, int32_t* height) {
+  std::vector<int32_t> lvl(sy.m, 0);
+  int32_t h = 0;
+  for (int32_t p = 0; p < sy.m; ++p) {
+    if (!sy.st[p].empty()) {
+      const int32_t par = sy.st[p][0];
+      lvl[par] = std::max(lvl[par], lvl[p] + 1);
+    }
+    h = std::max(h, lvl[p] + 1);
+  }
+  *height = sy.m ? h : 0;
+  return lvl;
+}
+
+template <typename T>
+s_status upload(T** dst, const std::vector<T>& v) {
+  SF_CUDA(cudaMalloc((void**)dst, sizeof(T) * std::max<size_t>(v.size(), 1)));
+  if (!v.empty()) SF_CUDA(cudaMemcpy(*dst, v.data(), sizeof(T) * v.size(), cudaMemcpyHostToDevice));
+  return S_OK;
+}
+
+// ---- host: elliptic functions for Eq. (ContInt) ------------------------------------------
+
+// K(m) = pi / (2 AGM(1, sqrt(1 - m))), 0 <= m < 1.
+double ellip_k(double m) {
+  double a = 1.0, b = std::sqrt(1.0 - m);
+  for (int it = 0; it < 64 && std::fabs(a - b) > 1e-16 * a; ++it) {
+    const double an = 0.5 * (a + b);
+    b = std::sqrt(a * b);
+    a = an;
+  }
+  return M_PI / (a + b);
+}
+
+// sn, cn, dn(u|m) by the descending arithmetic-geometric mean (Abramowitz and Stegun 16.4):
+// a_0 = 1, b_0 = sqrt(1-m), c_0 = sqrt(m); a_n, b_n the AGM steps, c_n = (a_{n-1} - b_{n-1})/2
+// until c_N is negligible; phi_N = 2^N a_N u and phi_{n-1} = (phi_n + asin(c_n sin(phi_n)/a_n))/2;
+// sn = sin phi_0, cn = cos phi_0, dn = cos phi_0 / cos(phi_1 - phi_0).
+void ellip_j(double u, double m, double* sn, double* cn, double* dn) {
+  if (m <= 0.0) {
+    *sn = std::sin(u);
+    *cn = std::cos(u);
+    *dn = 1.0;
+    return;
+  }
+  double a[40], c[40];
+  a[0] = 1.0;
+  double b = std::sqrt(1.0 - m);
+  c[0] = std::sqrt(m);
+  int n = 0;
+  while (n < 38 && std::fabs(c[n]) > 1e-16) {
+    a[n + 1] = 0.5 * (a[n] + b);
+    c[n + 1] = 0.5 * (a[n] - b);
+    b = std::sqrt(a[n] * b);
+    ++n;
+  }
+  double phi = std::ldexp(a[n] * u, n);
+  double prev = phi;
+  for (int j = n; j >= 1; --j) {
+    prev = phi;
+    phi = 0.5 * (phi + std::asin(c[j] * std::sin(phi) / a[j]));
+  }
+  *sn = std::sin(phi);
+  *cn = std::cos(phi);
+  *dn = n >= 1 ? *cn / std::cos(prev - phi) : 1.0;
+}
+
+}  // namespace
+}  // namespace sf
+
+using namespace sf;
+
+struct s_selinv_t {
+  const s_pattern_t* S = nullptr;
+  int32_t m = 0, height = 0, maxb = 0;
+  int64_t nl = 0, nent = 0;
+  double flops_factor = 0.0, flops_invert = 0.0;
+  // level lists (host offsets into the device arrays)
+  std::vector<int64_t> upd_ptr, off_ptr, sn_ptr;
+  std::vector<int32_t> lvl_slices;  // pivot CTAs per supernode on each level
+  // device
+  int32_t* bs = nullptr;
+  int64_t* colptr = nullptr;
+  int32_t* colrow = nullptr;
+  int64_t* loff = nullptr;
+  int64_t* rowptr = nullptr;
+  int32_t* rowcol = nullptr;
+  int32_t* rowblk = nullptr;
+  int64_t* aoff = nullptr;
+  SiItem* upd = nullptr;
+  SiItem* off = nullptr;
+  int32_t* sn = nullptr;
+  int32_t* s2l = nullptr;
+  int8_t* s2t = nullptr;
+  double* W = nullptr;
+  double* L = nullptr;
+  double* Z = nullptr;
+  unsigned int* flag = nullptr;
+  unsigned int* flag_host = nullptr;
+};
+
+static void selinv_free(s_selinv_t* p) {
+  cudaFree(p->bs);
+  cudaFree(p->colptr);
+  cudaFree(p->colrow);
+  cudaFree(p->loff);
+  cudaFree(p->rowptr);
+  cudaFree(p->rowcol);
+  cudaFree(p->rowblk);
+  cudaFree(p->aoff);
+  cudaFree(p->upd);
+  cudaFree(p->off);
+  cudaFree(p->sn);
+  cudaFree(p->s2l);
+  cudaFree(p->s2t);
+  cudaFree(p->W);
+  cudaFree(p->L);
+  cudaFree(p->Z);
+  if (p->flag_host) cudaFreeHost(p->flag_host);
+}
+
+static SiDev dev_of(const s_selinv_t* p) {
+  SiDev s;
+  s.bs = p->bs;
+  s.colptr = p->colptr;
+  s.colrow = p->colrow;
+  s.loff = p->loff;
+  s.rowptr = p->rowptr;
+  s.rowcol = p->rowcol;
+  s.rowblk = p->rowblk;
+  s.aoff = p->aoff;
+  s.W = p->W;
+  s.L = p->L;
+  s.Z = p->Z;
+  s.flag = p->flag;
+  return s;
+}
+
+static s_status selinv_build(s_selinv_t* p) {
+  const s_pattern_t* S = p->S;
+  const int32_t nc = (int32_t)S->bsize.size();
+  Symbolic sy;
+  s_status st = symbolic(nc, S->rowptr.data(), S->colidx.data(), S->bsize.data(), &sy);
+  if (st) return st;
+  const int32_t m = sy.m;
+  p->m = m;
+  std::vector<int32_t> lvl = etree_levels(sy, &p->height);
+  std::vector<int32_t> bs(std::max(m, 1), 0);
+  for (int32_t q = 0; q < m; ++q) {
+    bs[q] = S->bsize[sy.perm[q]];
+    if (bs[q] > kSiMaxB) return set_error(S_ERR_ARG, "selected inversion: blocks wider than 64");
+    p->maxb = std::max(p->maxb, bs[q]);
+  }
+  // CSC of L
+  std::vector<int64_t> colptr(m + 1, 0), loff;
+  std::vector<int32_t> colrow;
+  for (int32_t k = 0; k < m; ++k) colptr[k + 1] = colptr[k] + 1 + (int64_t)sy.st[k].size();
+  const int64_t nl = colptr[m];
+  if (nl >= INT32_MAX) return set_error(S_ERR_ARG, "selected inversion: factor has more than 2^31 blocks");
+  colrow.reserve(nl);
+  loff.reserve(nl + 1);
+  int64_t e = 0;
+  double ff = 0.0, fi = 0.0;
+  for (int32_t k = 0; k < m; ++k) {
+    colrow.push_back(k);
+    loff.push_back(e);
+    e += (int64_t)bs[k] * bs[k];
+    double T = 0.0, T2 = 0.0;
+    for (int32_t i : sy.st[k]) {
+      colrow.push_back(i);
+      loff.push_back(e);
+      e += (int64_t)bs[i] * bs[k];
+      T += bs[i];
+      T2 += (double)bs[i] * bs[i];
+    }
+    const double b = bs[k];
+    // update pairs (i >= i') of struct(k) and the pivot; inversion: struct(k) x struct(k)
+    ff += b * (T * T + T2) + 2.0 * b * b * b + 2.0 * b * b * T;
+    fi += 2.0 * b * T * T + 2.0 * b * b * T;
+  }
+  loff.push_back(e);
+  p->nl = nl;
+  p->nent = e;
+  p->flops_factor = ff;
+  p->flops_invert = fi;
+  // CSR of L: row i holds its columns ascending (the diagonal last)
+  std::vector<int64_t> rowptr(m + 1, 0);
+  for (int64_t q = 0; q < nl; ++q) ++rowptr[colrow[q] + 1];
+  for (int32_t i = 0; i < m; ++i) rowptr[i + 1] += rowptr[i];
+  std::vector<int32_t> rowcol(nl), rowblk(nl);
+  {
+    std::vector<int64_t> fill(rowptr.begin(), rowptr.end() - 1);
+    for (int32_t k = 0; k < m; ++k)
+      for (int64_t q = colptr[k]; q < colptr[k + 1]; ++q) {
+        const int32_t i = colrow[q];
+        rowcol[fill[i]] = k;
+        rowblk[fill[i]] = (int32_t)q;
+        ++fill[i];
+      }
+  }
+  // S blocks of each L block, and L blocks of each S block
+  std::vector<int64_t> aoff(nl, -1);
+  const int64_t snb = (int64_t)S->colidx.size();
+  std::vector<int32_t> s2l(std::max<int64_t>(snb, 1), -1);
+  std::vector<int8_t> s2t(std::max<int64_t>(snb, 1), 0);
+  for (int32_t r = 0; r < nc; ++r) {
+    for (int64_t b = S->rowptr[r]; b < S->rowptr[r + 1]; ++b) {
+      const int32_t c = S->colidx[b];
+      const int32_t pr = sy.pos[r], pc = sy.pos[c];
+      if (pr < 0 || pc < 0) continue;
+      const int32_t hi = std::max(pr, pc), lo = std::min(pr, pc);
+      const int32_t* f = std::lower_bound(colrow.data() + colptr[lo], colrow.data() + colptr[lo + 1], hi);
+      if (f == colrow.data() + colptr[lo + 1] || *f != hi)
+        return set_error(S_ERR_PATTERN, "selected inversion: internal error, S not inside the factor");
+      const int64_t q = f - colrow.data();
+      s2l[b] = (int32_t)q;
+      s2t[b] = pr < pc ? 1 : 0;
+      if (pr >= pc) aoff[q] = S->voff[b];
+    }
+  }
+  for (int32_t k = 0; k < m; ++k)
+    if (aoff[colptr[k]] < 0) return set_error(S_ERR_PATTERN, "selected inversion: pattern lacks a diagonal block");
+  // level lists
+  const int32_t H = p->height;
+  std::vector<std::vector<int32_t>> bylvl(H);
+  for (int32_t k = 0; k < m; ++k) bylvl[lvl[k]].push_back(k);
+  std::vector<SiItem> upd, off;
+  std::vector<int32_t> sn;
+  p->upd_ptr.assign(1, 0);
+  p->off_ptr.assign(1, 0);
+  p->sn_ptr.assign(1, 0);
+  p->lvl_slices.assign(H, 1);
+  for (int32_t l = 0; l < H; ++l) {
+    int64_t longest = 0;
+    for (int32_t k : bylvl[l]) {
+      sn.push_back(k);
+      longest = std::max<int64_t>(longest, colptr[k + 1] - colptr[k] - 1);
+      for (int64_t q = colptr[k]; q < colptr[k + 1]; ++q) {
+        const int ne = bs[colrow[q]] * bs[k];
+        for (int e0 = 0; e0 < ne; e0 += kSiTileEnt) {
+          upd.push_back(SiItem{(int32_t)q, k, e0});
+          if (q > colptr[k]) off.push_back(SiItem{(int32_t)q, k, e0});
+        }
+      }
+    }
+    p->lvl_slices[l] = (int32_t)std::max<int64_t>(1, (longest + kSiSlice - 1) / kSiSlice);
+    p->upd_ptr.push_back((int64_t)upd.size());
+    p->off_ptr.push_back((int64_t)off.size());
+    p->sn_ptr.push_back((int64_t)sn.size());
+  }
+  if ((st = upload(&p->bs, bs)) || (st = upload(&p->colptr, colptr)) || (st = upload(&p->colrow, colrow)) ||
+      (st = upload(&p->loff, loff)) || (st = upload(&p->rowptr, rowptr)) || (st = upload(&p->rowcol, rowcol)) ||
+      (st = upload(&p->rowblk, rowblk)) || (st = upload(&p->aoff, aoff)) || (st = upload(&p->upd, upd)) ||
+      (st = upload(&p->off, off)) || (st = upload(&p->sn, sn)) || (st = upload(&p->s2l, s2l)) ||
+      (st = upload(&p->s2t, s2t)))
+    return st;
+  const size_t vb = sizeof(double) * (size_t)std::max<int64_t>(e, 1);
+  cudaError_t ce = cudaMalloc(&p->W, vb);
+  if (ce == cudaSuccess) ce = cudaMalloc(&p->L, vb);
+  if (ce == cudaSuccess) ce = cudaMalloc(&p->Z, vb);
+  if (ce == cudaErrorMemoryAllocation) {
+    cudaGetLastError();
+    return set_error(S_ERR_NOMEM, "selected inversion: no device memory for the factor");
+  }
+  SF_CUDA(ce);
+  SF_CUDA(cudaHostAlloc((void**)&p->flag_host, sizeof(unsigned int), cudaHostAllocMapped));
+  *(volatile unsigned int*)p->flag_host = 0u;
+  SF_CUDA(cudaHostGetDevicePointer((void**)&p->flag, p->flag_host, 0));
+  return S_OK;
+}
+
+extern "C" {
+
+s_status s_selinv_order(int32_t n_clusters, const int64_t* rowptr, const int32_t* colidx, const int32_t* bsize,
+                        int32_t* perm, int64_t* l_blocks, int32_t* levels) {
+  if (n_clusters < 1 || !rowptr || !colidx || !bsize || !perm)
+    return set_error(S_ERR_ARG, "s_selinv_order: null argument or no clusters");
+  if (rowptr[0] != 0) return set_error(S_ERR_PATTERN, "s_selinv_order: rowptr[0] != 0");
+  for (int32_t r = 0; r < n_clusters; ++r)
+    if (rowptr[r + 1] < rowptr[r]) return set_error(S_ERR_PATTERN, "s_selinv_order: rowptr decreases");
+  Symbolic sy;
+  s_status st = symbolic(n_clusters, rowptr, colidx, bsize, &sy);
+  if (st) return st;
+  std::memcpy(perm, sy.perm.data(), sizeof(int32_t) * n_clusters);
+  int64_t nl = sy.m;
+  for (const auto& s : sy.st) nl += (int64_t)s.size();
+  if (l_blocks) *l_blocks = nl;
+  int32_t h = 0;
+  etree_levels(sy, &h);
+  if (levels) *levels = h;
+  return S_OK;
+}
+
+s_status s_selinv_create(s_pattern S, s_selinv* out) {
+  if (!S || !out) return set_error(S_ERR_ARG, "s_selinv_create: null argument");
+  s_selinv_t* p = new s_selinv_t();
+  p->S = S;
+  s_status st = selinv_build(p);
+  if (st) {
+    selinv_free(p);
+    delete p;
+    return st;
+  }
+  *out = p;
+  return S_OK;
+}
+
+s_status s_selinv_destroy(s_selinv p) {
+  if (!p) return S_OK;
+  selinv_free(p);
+  delete p;
+  return S_OK;
+}
+
+s_status s_selinv_stats(s_selinv p, int64_t* l_blocks, int64_t* l_entries, int32_t* levels, double* flops_factor,
+                        double* flops_invert) {
+  if (!p) return set_error(S_ERR_ARG, "s_selinv_stats: null plan");
+  if (l_blocks) *l_blocks = p->nl;
+  if (l_entries) *l_entries = p->nent;
+  if (levels) *levels = p->height;
+  if (flops_factor) *flops_factor = p->flops_factor;
+  if (flops_invert) *flops_invert = p->flops_invert;
+  return S_OK;
+}
+
+s_status s_selinv_factor(s_selinv p, const double* A, double sigma, void* stream) {
+  if (!p || (!A && p->S->d.nnz > 0)) return set_error(S_ERR_ARG, "s_selinv_factor: null argument");
+  if (p->m == 0) return S_OK;
+  cudaStream_t cs = (cudaStream_t)stream;
+  const SiDev s = dev_of(p);
+  const size_t smem = sizeof(double) * (size_t)p->maxb * p->maxb;
+  for (int32_t l = 0; l < p->height; ++l) {
+    const int64_t n = p->upd_ptr[l + 1] - p->upd_ptr[l];
+    if (n > 0) {
+      const int64_t grid = (n + kSiWarps - 1) / kSiWarps;
+      si_update_kernel<<<(unsigned)grid, kSiWarps * 32, 0, cs>>>(s, p->upd + p->upd_ptr[l], n, A, sigma);
+    }
+    const int64_t ns = p->sn_ptr[l + 1] - p->sn_ptr[l];
+    if (ns > 0) {
+      dim3 g((unsigned)ns, (unsigned)p->lvl_slices[l]);
+      si_pivot_kernel<<<g, kSiThreads, smem, cs>>>(s, p->sn + p->sn_ptr[l]);
+    }
+  }
+  SF_CUDA(cudaGetLastError());
+  return S_OK;
+}
+
+s_status s_selinv_invert(s_selinv p, double alpha, double beta, double* out, void* stream) {
+  if (!p || (!out && p->S->d.nnz > 0)) return set_error(S_ERR_ARG, "s_selinv_invert: null argument");
+  cudaStream_t cs = (cudaStream_t)stream;
+  if (p->m > 0) {
+    const SiDev s = dev_of(p);
+    for (int32_t l = p->height - 1; l >= 0; --l) {
+      const int64_t n = p->off_ptr[l + 1] - p->off_ptr[l];
+      if (n > 0) {
+        const int64_t grid = (n + kSiWarps - 1) / kSiWarps;
+        si_offdiag_kernel<<<(unsigned)grid, kSiWarps * 32, 0, cs>>>(s, p->off + p->off_ptr[l], n);
+      }
+      const int64_t ns = p->sn_ptr[l + 1] - p->sn_ptr[l];
+      if (ns > 0) si_diag_kernel<<<(unsigned)ns, kSiThreads, 0, cs>>>(s, p->sn + p->sn_ptr[l]);
+    }
+  }
+  const DevPattern& d = p->S->d;
+  if (d.nblocks > 0) {
+    const int64_t grid = std::min<int64_t>((d.nblocks * 32 + 255) / 256, (int64_t)sm_count() * 8);
+    si_scatter_kernel<<<(unsigned)std::max<int64_t>(grid, 1), 256, 0, cs>>>(
+        d.nblocks, d.bsize, d.brow, d.colidx, d.voff, p->s2l, p->s2t, p->loff, p->Z, alpha, beta, out);
+  }
+  SF_CUDA(cudaGetLastError());
+  return S_OK;
+}
+
+s_status s_selinv_status(s_selinv p, void* stream) {
+  if (!p) return set_error(S_ERR_ARG, "s_selinv_status: null plan");
+  SF_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
+  volatile unsigned int* w = p->flag_host;
+  if (w && *w) {
+    *w = 0u;
+    return set_error(S_ERR_NOT_SPD, "selected inversion: a pivot block was not positive definite");
+  }
+  return S_OK;
+}
+
+s_status s_contour_nodes(double c_lo, double c_hi, int32_t n, double* shifts, double* weights) {
+  if (!(c_lo > 0.0) || !(c_hi >= c_lo) || !std::isfinite(c_hi) || n < 1 || !shifts || !weights)
+    return set_error(S_ERR_ARG, "s_contour_nodes: need 0 < c_lo <= c_hi and n >= 1");
+  const double m = 1.0 - c_lo / c_hi;
+  const double K = ellip_k(m);
+  const double sc = std::sqrt(c_lo);
+  for (int32_t k = 0; k < n; ++k) {
+    const double t = K * (k + 0.5) / n;
+    double sn, cn, dn;
+    ellip_j(t, m, &sn, &cn, &dn);
+    const double w = sc * sn / cn;
+    shifts[k] = w * w;
+    weights[k] = 2.0 * K * sc / (M_PI * n) * dn / (cn * cn);
+  }
+  return S_OK;
+}
+
+s_status s_selinv_invsqrt(s_selinv p, const double* A, double c_lo, double c_hi, int32_t n, double* out,
+                          void* stream) {
+  if (!p || n < 1 || n > 1024) return set_error(S_ERR_ARG, "s_selinv_invsqrt: null plan or n outside 1..1024");
+  std::vector<double> w2(n), wt(n);
+  s_status st = s_contour_nodes(c_lo, c_hi, n, w2.data(), wt.data());
+  if (st) return st;
+  for (int32_t k = 0; k < n; ++k) {
+    if ((st = s_selinv_factor(p, A, w2[k], stream))) return st;
+    if ((st = s_selinv_invert(p, wt[k], k ? 1.0 : 0.0, out, stream))) return st;
+  }
+  return s_selinv_status(p, stream);
+}
+
+}  // extern "C"

@@ -15,6 +15,7 @@ LIB_PATH = os.path.join(HERE, "_lib", "libsformat.so")
 
 S_OK, S_ERR_ARG, S_ERR_PATTERN, S_ERR_MISMATCH, S_ERR_NOMEM, S_ERR_CUDA, S_ERR_NOT_CONVERGED, S_ERR_TIMEOUT = \
     0, -1, -2, -3, -4, -5, -6, -7
+S_ERR_NOT_SPD = -8
 S_FP64, S_FP32, S_BF16X3, S_FP64_DF, S_TF32X3 = 0, 1, 2, 3, 4
 S_SQRT, S_EXP, S_EXP_NEG = 0, 1, 2
 

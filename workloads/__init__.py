@@ -22,6 +22,11 @@ Sec. 5.3):
                       2D, 40 in 3D); N from 5,000 to 1,000,000 (PAPER_MULT_NS).  The second
                       factor is the first with every stored entry a scaled by (1 + 0.1 u),
                       u uniform in [0,1] (perturbation_factors).
+  selinv_2d           selected inversion (K + mu I)^{-1} on S (Sec. 4.2, 5.2): paper_mult_2d's
+                      points and kernel, mu in {1e-2, 1e-4, 1e-6}; N = 16384 by default.
+  contour_sphere      A^{1/2} by Eq. (ContInt) (Sec. 4.4, 5.3): N = 16384 on the unit sphere,
+                      exp(-2r)/N (Matern-1/2, ell = 0.5), q = 3, leaf 40, eta = 1.25,
+                      tau = 1e-5/N, A = K + 1e-4 I, c_lo = 1e-4, c_hi = 1, 7 nodes.
   pair_2d_4096        two kernels on one tree for a product of different matrices: N=4096
                       uniform [0,1]^2, q=2, leaf 16; A Matern-3/2 ell=0.2 on the eta=1.25
                       pattern, B Matern-5/2 ell=0.1 on the eta=1.0 pattern, C on the eta=0.8
@@ -73,6 +78,16 @@ PAPER_MULT = {
 }
 WORKLOADS.update(PAPER_MULT)
 
+# Selected inversion and the contour integral (Sec. 4.2-4.4 and the experiments of Sec. 5.2
+# and 5.3): the inversion experiment's uniform [0,1]^2 points and exp(-r)/N kernel, ridge mu
+# given at run time; the matrix-function experiment's exp(-2r)/N kernel (ell = 0.5) with
+# ridge mu = 1e-4 on a closed surface (the unit sphere standing in for the 3D scan).
+SELINV = {
+    "selinv_2d": Workload("selinv_2d", 8, 16384, 2, "cube", 0.5, 1.0, 0.0, 3, 20, 1.25, 1e-5),
+    "contour_sphere": Workload("contour_sphere", 9, 16384, 3, "sphere", 0.5, 0.5, 1e-4, 3, 40, 1.25, 1e-5),
+}
+WORKLOADS.update(SELINV)
+
 # Product of two different kernels on one tree (same points, leaf and q), three patterns:
 # (nu, ell, eta) of A, of B, and the eta of C's pattern.
 PAIR_2D = {"seed": 8, "n": 4096, "d": 2, "q": 2, "leaf": 16,
@@ -82,7 +97,7 @@ PAIR_2D = {"seed": 8, "n": 4096, "d": 2, "q": 2, "leaf": 16,
 def tau_of(w, n):
     """Absolute threshold of a workload at size n: the paper-benchmark workloads state tau
     relative to 1/N (tau = 1e-5/N), the others absolutely."""
-    return w.tau / n if w.name.startswith("paper_mult") else w.tau
+    return w.tau / n if w.name.startswith(("paper_mult", "selinv", "contour")) else w.tau
 
 
 def perturbation_factors(count, seed):
