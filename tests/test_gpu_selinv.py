@@ -24,6 +24,7 @@ from oracle import selinv as osel
 from oracle.pipeline import compress_kernel
 from oracle.sformat import BlockCSR
 from tests.gpu_util import dev, host, pattern_of, rel_frob
+from tests.test_gpu_product import drop_empty
 from tests.test_selinv_host import symmetric_pattern
 
 pytestmark = pytest.mark.gpu
@@ -45,7 +46,7 @@ def random_spd(bsize, density, seed):
     A = BlockCSR(bsize, rowptr, colidx)
     A.val[:] = rng.uniform(-1.0, 1.0, len(A.val))
     D = A.to_dense()
-    A = BlockCSR.from_dense(D + D.T, bsize, rowptr, colidx)
+    A = drop_empty(BlockCSR.from_dense(D + D.T, bsize, rowptr, colidx))   # no blocks of empty clusters
     sigma = float(np.abs(A.to_dense()).sum(axis=1).max()) + 1.0
     return A, sigma
 
