@@ -6,25 +6,34 @@
 // its samplets a dense block.  The host picks a minimum-degree elimination order of the
 // block graph of S, plays the elimination game to get the pattern of L (position space,
 // i >= k), and lists the blocks of every level of the elimination tree.  Blocks whose
-// columns sit on one level are independent, so each level is one launch:
+// columns sit on one level are independent, so each level is one launch per step:
 //
 //   factor, levels from the leaves up (A + sigma I = L D L^T, W = L D kept beside L):
 //     update  W(i,k) = A(i,k) + sigma [i = k] - sum_{j < k} W(i,j) L(k,j)^T over the j in
-//             both row i and row k of L (one warp per output block and 512-entry tile);
+//             both row i and row k of L;
 //     pivot   D(k,k) = W(k,k) inverted by Gauss-Jordan in shared memory (positive definite:
 //             no pivoting; a pivot that is not positive is recorded), then
 //             L(i,k) = W(i,k) D(k,k)^{-1} for the blocks of column k (a CTA per supernode
 //             and slice of its column), D^{-1} stored in L's diagonal block;
 //   inversion, levels from the root down (Takahashi-type recurrences from Eq. (blockInv)):
 //     off     Z(i,k) = - sum_{j in struct(k)} Z(i,j) L(j,k), Z(i,j) read from block
-//             (max, min) of Z, transposed when i < j (one warp per output block and tile);
+//             (max, min) of Z, transposed when i < j;
 //     diag    Z(k,k) = D(k,k)^{-1} - sum_{j in struct(k)} Z(j,k)^T L(j,k) (a CTA per
-//             supernode);
+//             supernode, its warps splitting the sum);
 //   scatter   out = alpha P_S(Z) + beta out, blocks of S read from Z or its transpose.
 //
-// Every entry an update reads was written by an earlier launch (descendants sit on lower
-// levels, ancestors on higher ones), so the kernels need no synchronisation beyond stream
-// order and no waits.
+// The update and off-diagonal steps give one warp an output block (512-entry tiles of it,
+// 16 entries per lane) and a share of its sum: near the root the elimination tree is a
+// chain whose levels hold few, long sums, so the host splits each sum into `split` strided
+// parts (split-K) to keep every SM sub-partition busy.  With split > 1 the parts land in a
+// scratch buffer and the next launch of the level (pivot, diag) adds them in a fixed order,
+// so results do not depend on scheduling.  The operand blocks of each term are staged in
+// shared memory 16 columns at a time with coalesced loads (row pitch 17 doubles: rows fall
+// in different banks), so a warp waits for one L2 round trip per slice, not per product.
+//
+// Every entry a launch reads was written by an earlier launch (descendants sit on lower
+// levels, ancestors on higher ones) or by its own CTA before a barrier, so the kernels need
+// no synchronisation beyond stream order and no waits.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -42,6 +51,9 @@ constexpr int kSiTileEnt = 32 * kSiEnt;   // entries of one work item
 constexpr int kSiWarps = 4;               // warps per CTA of the block kernels
 constexpr int kSiThreads = 128;           // threads of the pivot and diagonal kernels
 constexpr int kSiSlice = 8;               // column blocks per pivot CTA
+constexpr int kSiU = 16;                  // columns of t staged per slice
+constexpr int kSiUp = kSiU + 1;           // row pitch of a staged slice (doubles)
+constexpr int kSiMaxSplit = 16;           // parts of one split sum
 constexpr int kSiMaxClusters = 32768;     // non-empty clusters of the host bitset analysis
 
 struct SiItem {
@@ -55,6 +67,7 @@ struct SiDev {
   const int64_t* colptr;  // CSC of L: column k holds blocks colptr[k] .. colptr[k+1]-1,
   const int32_t* colrow;  //   the diagonal first, then the rows of struct(k) ascending
   const int64_t* loff;    // entry offset of each CSC block (rows x cols, row-major)
+  const int64_t* lpo;     // entry offset of each CSC block among the blocks of its level
   const int64_t* rowptr;  // CSR of L: row i holds columns ascending, the diagonal last
   const int32_t* rowcol;
   const int32_t* rowblk;  // CSC block of each CSR entry
@@ -63,7 +76,9 @@ struct SiDev {
   double* W;              // L D (D in the diagonal blocks)
   double* L;              // L (D^{-1} in the diagonal blocks)
   double* Z;              // the inverse on the pattern of L
+  double* P;              // partial sums of split launches: [part][entries of the level]
   unsigned int* flag;     // mapped host word: 1 = a pivot block was not positive definite
+  int maxb;               // widest block of the plan
 };
 
 __device__ __forceinline__ int64_t si_lower_bound(const int32_t* a, int64_t lo, int64_t hi, int32_t v) {
@@ -75,28 +90,79 @@ __device__ __forceinline__ int64_t si_lower_bound(const int32_t* a, int64_t lo, 
   return lo;
 }
 
-// factor update: W(i,k) = A(i,k) + sigma [i = k] - sum_j W(i,j) L(k,j)^T
+// Entry coordinates of a lane's kSiEnt entries of a rows x cols tile starting at e0.
+__device__ __forceinline__ void si_entries(int e0, int ne, int cols, int lane, int* rr, int* cc) {
+#pragma unroll
+  for (int m = 0; m < kSiEnt; ++m) {
+    const int e = e0 + lane + 32 * m;
+    rr[m] = e < ne ? e / cols : -1;
+    cc[m] = e < ne ? e - rr[m] * cols : 0;
+  }
+}
+
+// acc[m] += sign * sum_t a[rr[m]][t] b[cc[m]][t] over t < uw4 (staged, zero padded to 4).
+__device__ __forceinline__ void si_dot(const double* a, const double* b, int uw4, const int* rr, const int* cc,
+                                       double sign, double* acc) {
+#pragma unroll
+  for (int m = 0; m < kSiEnt; ++m) {
+    if (rr[m] < 0) continue;
+    const double* ar = a + rr[m] * kSiUp;
+    const double* br = b + cc[m] * kSiUp;
+    double t0 = 0.0, t1 = 0.0;
+    for (int t = 0; t < uw4; t += 4) {
+      t0 = fma(ar[t], br[t], t0);
+      t1 = fma(ar[t + 1], br[t + 1], t1);
+      t0 = fma(ar[t + 2], br[t + 2], t0);
+      t1 = fma(ar[t + 3], br[t + 3], t1);
+    }
+    acc[m] = fma(sign, t0 + t1, acc[m]);
+  }
+}
+
+// Stage rows x uw values into dst[r * kSiUp + t] (zero padded to uw4 columns):
+// value(r, t) = src[r * rs + t * ts] (rs, ts: the source's row and column strides).  Plain
+// (coherent) loads: the diagonal kernel reads blocks its own CTA wrote before a barrier.
+__device__ __forceinline__ void si_stage(double* dst, const double* src, int rows, int uw, int uw4, int rs, int ts,
+                                         int lane) {
+  if (ts == 1) {
+    for (int idx = lane; idx < rows * uw4; idx += 32) {
+      const int r = idx / uw4, t = idx - r * uw4;
+      dst[r * kSiUp + t] = t < uw ? src[(int64_t)r * rs + t] : 0.0;
+    }
+  } else {
+    for (int idx = lane; idx < rows * uw4; idx += 32) {  // rows fastest: coalesced when rs = 1
+      const int t = idx / rows, r = idx - t * rows;
+      dst[r * kSiUp + t] = t < uw ? src[(int64_t)t * ts + (int64_t)r * rs] : 0.0;
+    }
+  }
+}
+
+// factor update: W(i,k) = A(i,k) + sigma [i = k] - sum_j W(i,j) L(k,j)^T; warp gw serves
+// item gw / split and the part gw % split of its sum (32-candidate chunks of row k).
 __global__ void __launch_bounds__(kSiWarps * 32) si_update_kernel(SiDev s, const SiItem* __restrict__ items,
-                                                                   int64_t nitems, const double* __restrict__ A,
-                                                                   double sigma) {
-  const int lane = threadIdx.x & 31;
-  const int64_t wid = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-  if (wid >= nitems) return;
-  const SiItem it = items[wid];
+                                                                   int64_t nitems, int split, int64_t E,
+                                                                   const double* __restrict__ A, double sigma) {
+  extern __shared__ double sh[];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int64_t gw = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  if (gw >= nitems * split) return;
+  const int64_t itn = gw / split;
+  const int part = (int)(gw - itn * split);
+  const SiItem it = items[itn];
   const int i = s.colrow[it.blk], k = it.col;
   const int bi = s.bs[i], bk = s.bs[k];
   const int ne = bi * bk;
-  const int64_t ao = s.aoff[it.blk];
-  double acc[kSiEnt];
+  double* sa = sh + (size_t)w * 2 * s.maxb * kSiUp;
+  double* sb = sa + (size_t)s.maxb * kSiUp;
   int rr[kSiEnt], cc[kSiEnt];
+  si_entries(it.e0, ne, bk, lane, rr, cc);
+  double acc[kSiEnt];
+  const int64_t ao = s.aoff[it.blk];
 #pragma unroll
   for (int m = 0; m < kSiEnt; ++m) {
-    const int e = it.e0 + lane + 32 * m;
-    rr[m] = e < ne ? e / bk : -1;
-    cc[m] = e < ne ? e - rr[m] * bk : 0;
     double v = 0.0;
-    if (e < ne) {
-      if (ao >= 0) v = A[ao + e];
+    if (part == 0 && rr[m] >= 0) {
+      if (ao >= 0) v = A[ao + it.e0 + lane + 32 * m];
       if (i == k && rr[m] == cc[m]) v += sigma;
     }
     acc[m] = v;
@@ -105,7 +171,7 @@ __global__ void __launch_bounds__(kSiWarps * 32) si_update_kernel(SiDev s, const
   const int64_t ri1 = s.rowptr[i + 1];
   const int64_t rk0 = s.rowptr[k], rk1 = s.rowptr[k + 1] - 1;
   int64_t lo = s.rowptr[i];
-  for (int64_t base = rk0; base < rk1; base += 32) {
+  for (int64_t base = rk0 + 32 * (int64_t)part; base < rk1; base += 32 * (int64_t)split) {
     const int64_t q = base + lane;
     const int32_t j = q < rk1 ? __ldg(s.rowcol + q) : INT32_MAX;
     const int64_t a = si_lower_bound(s.rowcol, lo, ri1, j);
@@ -118,23 +184,20 @@ __global__ void __launch_bounds__(kSiWarps * 32) si_update_kernel(SiDev s, const
       const int src = __ffs(mask) - 1;
       mask &= mask - 1u;
       const int jj = __shfl_sync(0xffffffffu, j, src);
-      const int64_t wo = s.loff[__shfl_sync(0xffffffffu, bij, src)];
-      const int64_t lo2 = s.loff[__shfl_sync(0xffffffffu, bkj, src)];
+      const double* Wij = s.W + s.loff[__shfl_sync(0xffffffffu, bij, src)];  // bi x bj
+      const double* Lkj = s.L + s.loff[__shfl_sync(0xffffffffu, bkj, src)];  // bk x bj
       const int bj = s.bs[jj];
-      const double* __restrict__ Wij = s.W + wo;   // bi x bj
-      const double* __restrict__ Lkj = s.L + lo2;  // bk x bj
-#pragma unroll
-      for (int m = 0; m < kSiEnt; ++m) {
-        if (rr[m] < 0) continue;
-        const double* wr = Wij + (int64_t)rr[m] * bj;
-        const double* lr = Lkj + (int64_t)cc[m] * bj;
-        double t = 0.0;
-        for (int u = 0; u < bj; ++u) t = fma(wr[u], lr[u], t);
-        acc[m] -= t;
+      for (int u0 = 0; u0 < bj; u0 += kSiU) {
+        const int uw = min(kSiU, bj - u0), uw4 = (uw + 3) & ~3;
+        __syncwarp();
+        si_stage(sa, Wij + u0, bi, uw, uw4, bj, 1, lane);
+        si_stage(sb, Lkj + u0, bk, uw, uw4, bj, 1, lane);
+        __syncwarp();
+        si_dot(sa, sb, uw4, rr, cc, -1.0, acc);
       }
     }
   }
-  double* out = s.W + s.loff[it.blk];
+  double* out = split > 1 ? s.P + (int64_t)part * E + s.lpo[it.blk] : s.W + s.loff[it.blk];
 #pragma unroll
   for (int m = 0; m < kSiEnt; ++m)
     if (rr[m] >= 0) out[it.e0 + lane + 32 * m] = acc[m];
@@ -163,9 +226,22 @@ __device__ bool si_gauss_jordan(double* M, int bk, double* prow, double* pcol) {
   return ok;
 }
 
+// Entry `idx` of CSC block q after the update of its level: W itself, or the sum of the
+// `split` parts in part order.
+__device__ __forceinline__ double si_assembled(const SiDev& s, const double* base, int64_t q, int idx, int split,
+                                               int64_t E) {
+  if (split <= 1) return base[s.loff[q] + idx];
+  const double* p = s.P + s.lpo[q] + idx;
+  double v = p[0];
+  for (int t = 1; t < split; ++t) v += p[(int64_t)t * E];
+  return v;
+}
+
 // pivot: D(k,k)^{-1} and L(i,k) = W(i,k) D(k,k)^{-1}; CTA (x, y) serves supernode sn[x] and
-// the column blocks y*kSiSlice+1 .. of it; slice 0 stores D^{-1}.
-__global__ void __launch_bounds__(kSiThreads) si_pivot_kernel(SiDev s, const int32_t* __restrict__ sn) {
+// the column blocks y*kSiSlice+1 .. of it; slice 0 stores D^{-1}.  With split > 1 the blocks
+// are first assembled from the update's parts (and W(i,k) stored).
+__global__ void __launch_bounds__(kSiThreads) si_pivot_kernel(SiDev s, const int32_t* __restrict__ sn, int split,
+                                                              int64_t E) {
   extern __shared__ double smem[];
   __shared__ double prow[kSiMaxB], pcol[kSiMaxB];
   const int k = sn[blockIdx.x];
@@ -174,8 +250,8 @@ __global__ void __launch_bounds__(kSiThreads) si_pivot_kernel(SiDev s, const int
   const int64_t q0 = c0 + 1 + (int64_t)blockIdx.y * kSiSlice;
   if (blockIdx.y > 0 && q0 >= c1) return;
   double* M = smem;
-  const double* D = s.W + s.loff[c0];
-  for (int idx = threadIdx.x; idx < bk * bk; idx += blockDim.x) M[idx] = D[idx];
+  double* Wb = smem + (size_t)s.maxb * s.maxb;
+  for (int idx = threadIdx.x; idx < bk * bk; idx += blockDim.x) M[idx] = si_assembled(s, s.W, c0, idx, split, E);
   __syncthreads();
   const bool ok = si_gauss_jordan(M, bk, prow, pcol);
   if (blockIdx.y == 0) {
@@ -189,39 +265,48 @@ __global__ void __launch_bounds__(kSiThreads) si_pivot_kernel(SiDev s, const int
   const int64_t q1 = min(c1, q0 + kSiSlice);
   for (int64_t q = q0; q < q1; ++q) {
     const int bi = s.bs[s.colrow[q]];
-    const double* Wq = s.W + s.loff[q];
+    double* Wq = s.W + s.loff[q];
+    for (int idx = threadIdx.x; idx < bi * bk; idx += blockDim.x) {
+      const double v = si_assembled(s, s.W, q, idx, split, E);
+      Wb[idx] = v;
+      if (split > 1) Wq[idx] = v;
+    }
+    __syncthreads();
     double* Lq = s.L + s.loff[q];
     for (int idx = threadIdx.x; idx < bi * bk; idx += blockDim.x) {
       const int r = idx / bk, c = idx - r * bk;
-      const double* wr = Wq + (int64_t)r * bk;
+      const double* wr = Wb + r * bk;
       double t = 0.0;
       for (int u = 0; u < bk; ++u) t = fma(wr[u], M[u * bk + c], t);
       Lq[idx] = t;
     }
+    __syncthreads();
   }
 }
 
-// inversion, off-diagonal blocks: Z(i,k) = - sum_{j in struct(k)} Z(i,j) L(j,k)
+// inversion, off-diagonal blocks: Z(i,k) = - sum_{j in struct(k)} Z(i,j) L(j,k); warp gw
+// serves item gw / split and the part gw % split of struct(k) (32-entry chunks).
 __global__ void __launch_bounds__(kSiWarps * 32) si_offdiag_kernel(SiDev s, const SiItem* __restrict__ items,
-                                                                    int64_t nitems) {
-  const int lane = threadIdx.x & 31;
-  const int64_t wid = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-  if (wid >= nitems) return;
-  const SiItem it = items[wid];
+                                                                    int64_t nitems, int split, int64_t E) {
+  extern __shared__ double sh[];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int64_t gw = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  if (gw >= nitems * split) return;
+  const int64_t itn = gw / split;
+  const int part = (int)(gw - itn * split);
+  const SiItem it = items[itn];
   const int i = s.colrow[it.blk], k = it.col;
   const int bi = s.bs[i], bk = s.bs[k];
   const int ne = bi * bk;
-  double acc[kSiEnt];
+  double* sa = sh + (size_t)w * 2 * s.maxb * kSiUp;
+  double* sb = sa + (size_t)s.maxb * kSiUp;
   int rr[kSiEnt], cc[kSiEnt];
+  si_entries(it.e0, ne, bk, lane, rr, cc);
+  double acc[kSiEnt];
 #pragma unroll
-  for (int m = 0; m < kSiEnt; ++m) {
-    const int e = it.e0 + lane + 32 * m;
-    rr[m] = e < ne ? e / bk : -1;
-    cc[m] = e < ne ? e - rr[m] * bk : 0;
-    acc[m] = 0.0;
-  }
+  for (int m = 0; m < kSiEnt; ++m) acc[m] = 0.0;
   const int64_t q0 = s.colptr[k] + 1, q1 = s.colptr[k + 1];
-  for (int64_t base = q0; base < q1; base += 32) {
+  for (int64_t base = q0 + 32 * (int64_t)part; base < q1; base += 32 * (int64_t)split) {
     const int64_t q = base + lane;
     const bool valid = q < q1;
     const int j = valid ? __ldg(s.colrow + q) : 0;
@@ -241,46 +326,80 @@ __global__ void __launch_bounds__(kSiWarps * 32) si_offdiag_kernel(SiDev s, cons
       const int zz = __shfl_sync(0xffffffffu, zb, src);
       const int64_t qq = base + src;
       const int bj = s.bs[jj];
-      const bool tr = i < jj;                          // Z(i,j) = Z(j,i)^T
-      const double* __restrict__ Zp = s.Z + s.loff[zz];  // bi x bj, or bj x bi when tr
-      const double* __restrict__ Ljk = s.L + s.loff[qq]; // bj x bk
-#pragma unroll
-      for (int m = 0; m < kSiEnt; ++m) {
-        if (rr[m] < 0) continue;
-        double t = 0.0;
-        if (tr) {
-          for (int u = 0; u < bj; ++u) t = fma(Zp[(int64_t)u * bi + rr[m]], Ljk[(int64_t)u * bk + cc[m]], t);
-        } else {
-          const double* zr = Zp + (int64_t)rr[m] * bj;
-          for (int u = 0; u < bj; ++u) t = fma(zr[u], Ljk[(int64_t)u * bk + cc[m]], t);
-        }
-        acc[m] -= t;
+      const bool tr = i < jj;                    // Z(i,j) = Z(j,i)^T
+      const double* Zp = s.Z + s.loff[zz];       // bi x bj, or bj x bi when tr
+      const double* Ljk = s.L + s.loff[qq];      // bj x bk
+      for (int u0 = 0; u0 < bj; u0 += kSiU) {
+        const int uw = min(kSiU, bj - u0), uw4 = (uw + 3) & ~3;
+        __syncwarp();
+        if (tr) si_stage(sa, Zp + (int64_t)u0 * bi, bi, uw, uw4, 1, bi, lane);
+        else si_stage(sa, Zp + u0, bi, uw, uw4, bj, 1, lane);
+        si_stage(sb, Ljk + (int64_t)u0 * bk, bk, uw, uw4, 1, bk, lane);
+        __syncwarp();
+        si_dot(sa, sb, uw4, rr, cc, -1.0, acc);
       }
     }
   }
-  double* out = s.Z + s.loff[it.blk];
+  double* out = split > 1 ? s.P + (int64_t)part * E + s.lpo[it.blk] : s.Z + s.loff[it.blk];
 #pragma unroll
   for (int m = 0; m < kSiEnt; ++m)
     if (rr[m] >= 0) out[it.e0 + lane + 32 * m] = acc[m];
 }
 
-// inversion, diagonal blocks: Z(k,k) = D^{-1} - sum_{j in struct(k)} Z(j,k)^T L(j,k)
-__global__ void __launch_bounds__(kSiThreads) si_diag_kernel(SiDev s, const int32_t* __restrict__ sn) {
+// inversion, diagonal blocks: (with split > 1, first Z(i,k) of the column from the parts)
+// Z(k,k) = D^{-1} - sum_{j in struct(k)} Z(j,k)^T L(j,k), the sum split over the CTA's warps
+// and added in warp order.
+__global__ void __launch_bounds__(kSiWarps * 32) si_diag_kernel(SiDev s, const int32_t* __restrict__ sn, int split,
+                                                                int64_t E) {
+  extern __shared__ double sh[];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int k = sn[blockIdx.x];
   const int bk = s.bs[k];
   const int64_t c0 = s.colptr[k], c1 = s.colptr[k + 1];
+  if (split > 1 && c1 > c0 + 1) {
+    const int64_t z0 = s.loff[c0 + 1], len = s.loff[c1] - z0;
+    const double* p = s.P + s.lpo[c0 + 1];
+    for (int64_t idx = threadIdx.x; idx < len; idx += blockDim.x) {
+      double v = p[idx];
+      for (int t = 1; t < split; ++t) v += p[(int64_t)t * E + idx];
+      s.Z[z0 + idx] = v;
+    }
+    __syncthreads();
+  }
+  double* sa = sh + (size_t)w * 2 * s.maxb * kSiUp;
+  double* sb = sa + (size_t)s.maxb * kSiUp;
+  double* red = sh + (size_t)kSiWarps * 2 * s.maxb * kSiUp;  // [warp][kSiTileEnt]
   const double* Dinv = s.L + s.loff[c0];
   double* Zkk = s.Z + s.loff[c0];
-  for (int idx = threadIdx.x; idx < bk * bk; idx += blockDim.x) {
-    const int r = idx / bk, c = idx - r * bk;
-    double t = 0.0;
-    for (int64_t q = c0 + 1; q < c1; ++q) {
+  const int ne = bk * bk;
+  for (int e0 = 0; e0 < ne; e0 += kSiTileEnt) {
+    int rr[kSiEnt], cc[kSiEnt];
+    si_entries(e0, ne, bk, lane, rr, cc);
+    double acc[kSiEnt];
+#pragma unroll
+    for (int m = 0; m < kSiEnt; ++m) acc[m] = 0.0;
+    for (int64_t q = c0 + 1 + w; q < c1; q += kSiWarps) {
       const int bj = s.bs[s.colrow[q]];
       const double* Zq = s.Z + s.loff[q];  // bj x bk
       const double* Lq = s.L + s.loff[q];
-      for (int u = 0; u < bj; ++u) t = fma(Zq[(int64_t)u * bk + r], Lq[(int64_t)u * bk + c], t);
+      for (int u0 = 0; u0 < bj; u0 += kSiU) {
+        const int uw = min(kSiU, bj - u0), uw4 = (uw + 3) & ~3;
+        __syncwarp();
+        si_stage(sa, Zq + (int64_t)u0 * bk, bk, uw, uw4, 1, bk, lane);
+        si_stage(sb, Lq + (int64_t)u0 * bk, bk, uw, uw4, 1, bk, lane);
+        __syncwarp();
+        si_dot(sa, sb, uw4, rr, cc, 1.0, acc);
+      }
     }
-    Zkk[idx] = Dinv[idx] - t;
+#pragma unroll
+    for (int m = 0; m < kSiEnt; ++m) red[w * kSiTileEnt + lane + 32 * m] = acc[m];
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < kSiTileEnt && e0 + idx < ne; idx += blockDim.x) {
+      double v = red[idx];
+      for (int t = 1; t < kSiWarps; ++t) v += red[t * kSiTileEnt + idx];
+      Zkk[e0 + idx] = Dinv[e0 + idx] - v;
+    }
+    __syncthreads();
   }
 }
 
@@ -499,6 +618,8 @@ struct s_selinv_t {
   // level lists (host offsets into the device arrays)
   std::vector<int64_t> upd_ptr, off_ptr, sn_ptr;
   std::vector<int32_t> lvl_slices;  // pivot CTAs per supernode on each level
+  std::vector<int64_t> lvl_ent;     // entries of the blocks of each level's columns
+  std::vector<int32_t> upd_split, off_split;  // parts of the update and off-diagonal sums
   // device
   int32_t* bs = nullptr;
   int64_t* colptr = nullptr;
@@ -508,6 +629,8 @@ struct s_selinv_t {
   int32_t* rowcol = nullptr;
   int32_t* rowblk = nullptr;
   int64_t* aoff = nullptr;
+  int64_t* lpo = nullptr;
+  double* P = nullptr;
   SiItem* upd = nullptr;
   SiItem* off = nullptr;
   int32_t* sn = nullptr;
@@ -529,6 +652,8 @@ static void selinv_free(s_selinv_t* p) {
   cudaFree(p->rowcol);
   cudaFree(p->rowblk);
   cudaFree(p->aoff);
+  cudaFree(p->lpo);
+  cudaFree(p->P);
   cudaFree(p->upd);
   cudaFree(p->off);
   cudaFree(p->sn);
@@ -550,10 +675,13 @@ static SiDev dev_of(const s_selinv_t* p) {
   s.rowcol = p->rowcol;
   s.rowblk = p->rowblk;
   s.aoff = p->aoff;
+  s.lpo = p->lpo;
   s.W = p->W;
   s.L = p->L;
   s.Z = p->Z;
+  s.P = p->P;
   s.flag = p->flag;
+  s.maxb = p->maxb;
   return s;
 }
 
@@ -641,29 +769,51 @@ static s_status selinv_build(s_selinv_t* p) {
   }
   for (int32_t k = 0; k < m; ++k)
     if (aoff[colptr[k]] < 0) return set_error(S_ERR_PATTERN, "selected inversion: pattern lacks a diagonal block");
-  // level lists
+  // level lists, level-local entry offsets, and the split of each level's long sums
   const int32_t H = p->height;
   std::vector<std::vector<int32_t>> bylvl(H);
   for (int32_t k = 0; k < m; ++k) bylvl[lvl[k]].push_back(k);
   std::vector<SiItem> upd, off;
   std::vector<int32_t> sn;
+  std::vector<int64_t> lpo(nl, 0);
   p->upd_ptr.assign(1, 0);
   p->off_ptr.assign(1, 0);
   p->sn_ptr.assign(1, 0);
   p->lvl_slices.assign(H, 1);
+  p->lvl_ent.assign(H, 0);
+  p->upd_split.assign(H, 1);
+  p->off_split.assign(H, 1);
+  const int64_t target = 2LL * kSiWarps * sm_count();  // two warps per SM sub-partition
+  int64_t scratch = 0;
   for (int32_t l = 0; l < H; ++l) {
-    int64_t longest = 0;
+    int64_t longest = 0, ent = 0, maxrow = 0;
+    const int64_t u0 = (int64_t)upd.size(), o0 = (int64_t)off.size();
     for (int32_t k : bylvl[l]) {
       sn.push_back(k);
       longest = std::max<int64_t>(longest, colptr[k + 1] - colptr[k] - 1);
+      maxrow = std::max<int64_t>(maxrow, rowptr[k + 1] - rowptr[k] - 1);
       for (int64_t q = colptr[k]; q < colptr[k + 1]; ++q) {
         const int ne = bs[colrow[q]] * bs[k];
+        lpo[q] = ent;
+        ent += ne;
         for (int e0 = 0; e0 < ne; e0 += kSiTileEnt) {
           upd.push_back(SiItem{(int32_t)q, k, e0});
           if (q > colptr[k]) off.push_back(SiItem{(int32_t)q, k, e0});
         }
       }
     }
+    const int64_t nu = (int64_t)upd.size() - u0, no = (int64_t)off.size() - o0;
+    auto choose = [&](int64_t items, int64_t len) {
+      int64_t sp = items > 0 ? (target + items - 1) / items : 1;
+      sp = std::min<int64_t>(sp, std::min<int64_t>(kSiMaxSplit, (len + 31) / 32));
+      while (sp > 1 && sp * ent > (int64_t)1 << 27) --sp;  // scratch at most 1 GiB
+      return (int32_t)std::max<int64_t>(1, sp);
+    };
+    p->upd_split[l] = choose(nu, maxrow);
+    p->off_split[l] = choose(no, longest);
+    const int32_t sp = std::max(p->upd_split[l], p->off_split[l]);
+    if (sp > 1) scratch = std::max<int64_t>(scratch, (int64_t)sp * ent);
+    p->lvl_ent[l] = ent;
     p->lvl_slices[l] = (int32_t)std::max<int64_t>(1, (longest + kSiSlice - 1) / kSiSlice);
     p->upd_ptr.push_back((int64_t)upd.size());
     p->off_ptr.push_back((int64_t)off.size());
@@ -671,7 +821,8 @@ static s_status selinv_build(s_selinv_t* p) {
   }
   if ((st = upload(&p->bs, bs)) || (st = upload(&p->colptr, colptr)) || (st = upload(&p->colrow, colrow)) ||
       (st = upload(&p->loff, loff)) || (st = upload(&p->rowptr, rowptr)) || (st = upload(&p->rowcol, rowcol)) ||
-      (st = upload(&p->rowblk, rowblk)) || (st = upload(&p->aoff, aoff)) || (st = upload(&p->upd, upd)) ||
+      (st = upload(&p->rowblk, rowblk)) || (st = upload(&p->aoff, aoff)) || (st = upload(&p->lpo, lpo)) ||
+      (st = upload(&p->upd, upd)) ||
       (st = upload(&p->off, off)) || (st = upload(&p->sn, sn)) || (st = upload(&p->s2l, s2l)) ||
       (st = upload(&p->s2t, s2t)))
     return st;
@@ -679,6 +830,7 @@ static s_status selinv_build(s_selinv_t* p) {
   cudaError_t ce = cudaMalloc(&p->W, vb);
   if (ce == cudaSuccess) ce = cudaMalloc(&p->L, vb);
   if (ce == cudaSuccess) ce = cudaMalloc(&p->Z, vb);
+  if (ce == cudaSuccess && scratch > 0) ce = cudaMalloc(&p->P, sizeof(double) * (size_t)scratch);
   if (ce == cudaErrorMemoryAllocation) {
     cudaGetLastError();
     return set_error(S_ERR_NOMEM, "selected inversion: no device memory for the factor");
@@ -744,22 +896,41 @@ s_status s_selinv_stats(s_selinv p, int64_t* l_blocks, int64_t* l_entries, int32
   return S_OK;
 }
 
+// Dynamic shared memory of the block kernels (per-warp staging of two operand slices, and
+// the diagonal kernel's warp sums) and of the pivot kernel (D^{-1} and one W block).
+static size_t stage_bytes(const s_selinv_t* p) { return sizeof(double) * (size_t)kSiWarps * 2 * p->maxb * kSiUp; }
+static size_t diag_bytes(const s_selinv_t* p) {
+  return stage_bytes(p) + sizeof(double) * (size_t)kSiWarps * kSiTileEnt;
+}
+static size_t pivot_bytes(const s_selinv_t* p) { return sizeof(double) * 2 * (size_t)p->maxb * p->maxb; }
+
+static s_status set_smem(const void* fn, size_t bytes) {
+  if (bytes > 48 * 1024) SF_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+  return S_OK;
+}
+
 s_status s_selinv_factor(s_selinv p, const double* A, double sigma, void* stream) {
   if (!p || (!A && p->S->d.nnz > 0)) return set_error(S_ERR_ARG, "s_selinv_factor: null argument");
   if (p->m == 0) return S_OK;
   cudaStream_t cs = (cudaStream_t)stream;
   const SiDev s = dev_of(p);
-  const size_t smem = sizeof(double) * (size_t)p->maxb * p->maxb;
+  s_status st;
+  if ((st = set_smem((const void*)si_update_kernel, stage_bytes(p))) ||
+      (st = set_smem((const void*)si_pivot_kernel, pivot_bytes(p))))
+    return st;
   for (int32_t l = 0; l < p->height; ++l) {
     const int64_t n = p->upd_ptr[l + 1] - p->upd_ptr[l];
+    const int split = p->upd_split[l];
     if (n > 0) {
-      const int64_t grid = (n + kSiWarps - 1) / kSiWarps;
-      si_update_kernel<<<(unsigned)grid, kSiWarps * 32, 0, cs>>>(s, p->upd + p->upd_ptr[l], n, A, sigma);
+      const int64_t grid = (n * split + kSiWarps - 1) / kSiWarps;
+      si_update_kernel<<<(unsigned)grid, kSiWarps * 32, stage_bytes(p), cs>>>(s, p->upd + p->upd_ptr[l], n, split,
+                                                                              p->lvl_ent[l], A, sigma);
     }
     const int64_t ns = p->sn_ptr[l + 1] - p->sn_ptr[l];
     if (ns > 0) {
       dim3 g((unsigned)ns, (unsigned)p->lvl_slices[l]);
-      si_pivot_kernel<<<g, kSiThreads, smem, cs>>>(s, p->sn + p->sn_ptr[l]);
+      si_pivot_kernel<<<g, kSiThreads, pivot_bytes(p), cs>>>(s, p->sn + p->sn_ptr[l], n > 0 ? split : 1,
+                                                             p->lvl_ent[l]);
     }
   }
   SF_CUDA(cudaGetLastError());
@@ -771,14 +942,22 @@ s_status s_selinv_invert(s_selinv p, double alpha, double beta, double* out, voi
   cudaStream_t cs = (cudaStream_t)stream;
   if (p->m > 0) {
     const SiDev s = dev_of(p);
+    s_status st;
+    if ((st = set_smem((const void*)si_offdiag_kernel, stage_bytes(p))) ||
+        (st = set_smem((const void*)si_diag_kernel, diag_bytes(p))))
+      return st;
     for (int32_t l = p->height - 1; l >= 0; --l) {
       const int64_t n = p->off_ptr[l + 1] - p->off_ptr[l];
+      const int split = n > 0 ? p->off_split[l] : 1;
       if (n > 0) {
-        const int64_t grid = (n + kSiWarps - 1) / kSiWarps;
-        si_offdiag_kernel<<<(unsigned)grid, kSiWarps * 32, 0, cs>>>(s, p->off + p->off_ptr[l], n);
+        const int64_t grid = (n * split + kSiWarps - 1) / kSiWarps;
+        si_offdiag_kernel<<<(unsigned)grid, kSiWarps * 32, stage_bytes(p), cs>>>(s, p->off + p->off_ptr[l], n,
+                                                                                 split, p->lvl_ent[l]);
       }
       const int64_t ns = p->sn_ptr[l + 1] - p->sn_ptr[l];
-      if (ns > 0) si_diag_kernel<<<(unsigned)ns, kSiThreads, 0, cs>>>(s, p->sn + p->sn_ptr[l]);
+      if (ns > 0)
+        si_diag_kernel<<<(unsigned)ns, kSiWarps * 32, diag_bytes(p), cs>>>(s, p->sn + p->sn_ptr[l], split,
+                                                                            p->lvl_ent[l]);
     }
   }
   const DevPattern& d = p->S->d;
