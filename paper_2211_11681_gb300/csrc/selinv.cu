@@ -167,17 +167,22 @@ __global__ void __launch_bounds__(kSiWarps * 32) si_update_kernel(SiDev s, const
     }
     acc[m] = v;
   }
-  // j over row k of L below the diagonal, matched in row i
-  const int64_t ri1 = s.rowptr[i + 1];
+  // j < k in both row i and row k of L: candidates from the shorter list (row k below its
+  // diagonal, or row i below column k), matched by binary search in the other
   const int64_t rk0 = s.rowptr[k], rk1 = s.rowptr[k + 1] - 1;
-  int64_t lo = s.rowptr[i];
-  for (int64_t base = rk0 + 32 * (int64_t)part; base < rk1; base += 32 * (int64_t)split) {
+  const int64_t ri0 = s.rowptr[i];
+  const int64_t ri1 = i == k ? rk1 : si_lower_bound(s.rowcol, ri0, s.rowptr[i + 1], k);
+  const bool from_k = rk1 - rk0 <= ri1 - ri0;
+  const int64_t c0 = from_k ? rk0 : ri0, c1 = from_k ? rk1 : ri1;  // candidates
+  const int64_t m1 = from_k ? ri1 : rk1;                           // searched list [lo, m1)
+  int64_t lo = from_k ? ri0 : rk0;
+  for (int64_t base = c0 + 32 * (int64_t)part; base < c1; base += 32 * (int64_t)split) {
     const int64_t q = base + lane;
-    const int32_t j = q < rk1 ? __ldg(s.rowcol + q) : INT32_MAX;
-    const int64_t a = si_lower_bound(s.rowcol, lo, ri1, j);
-    const bool hit = q < rk1 && a < ri1 && __ldg(s.rowcol + a) == j;
-    const int bij = hit ? __ldg(s.rowblk + a) : 0;
-    const int bkj = hit ? __ldg(s.rowblk + q) : 0;
+    const int32_t j = q < c1 ? __ldg(s.rowcol + q) : INT32_MAX;
+    const int64_t a = si_lower_bound(s.rowcol, lo, m1, j);
+    const bool hit = q < c1 && a < m1 && __ldg(s.rowcol + a) == j;
+    const int bij = hit ? __ldg(s.rowblk + (from_k ? a : q)) : 0;
+    const int bkj = hit ? __ldg(s.rowblk + (from_k ? q : a)) : 0;
     unsigned int mask = __ballot_sync(0xffffffffu, hit);
     lo = __shfl_sync(0xffffffffu, a, 31);
     while (mask) {
@@ -346,19 +351,25 @@ __global__ void __launch_bounds__(kSiWarps * 32) si_offdiag_kernel(SiDev s, cons
     if (rr[m] >= 0) out[it.e0 + lane + 32 * m] = acc[m];
 }
 
-// inversion, diagonal blocks: (with split > 1, first Z(i,k) of the column from the parts)
-// Z(k,k) = D^{-1} - sum_{j in struct(k)} Z(j,k)^T L(j,k), the sum split over the CTA's warps
-// and added in warp order.
+// inversion, diagonal blocks: Z(k,k) = D^{-1} - sum_{j in struct(k)} Z(j,k)^T L(j,k).  CTA
+// (x, y) serves supernode sn[x] and the column blocks y*kSiSlice+1 .. of it: with split > 1
+// it first assembles those Z(j,k) from the off-diagonal parts, then its warps split the
+// slice's terms and add them in warp order.  With one slice the CTA writes Z(k,k); with
+// several, each slice stores its sum in Q and the last slice to finish (counted per
+// supernode in `cnt`, which it resets) adds the slices in slice order and writes Z(k,k).
 __global__ void __launch_bounds__(kSiWarps * 32) si_diag_kernel(SiDev s, const int32_t* __restrict__ sn, int split,
-                                                                int64_t E) {
+                                                                int64_t E, int slices, unsigned int* cnt,
+                                                                double* Q) {
   extern __shared__ double sh[];
+  __shared__ int last;
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int k = sn[blockIdx.x];
   const int bk = s.bs[k];
   const int64_t c0 = s.colptr[k], c1 = s.colptr[k + 1];
-  if (split > 1 && c1 > c0 + 1) {
-    const int64_t z0 = s.loff[c0 + 1], len = s.loff[c1] - z0;
-    const double* p = s.P + s.lpo[c0 + 1];
+  const int64_t qs = c0 + 1 + (int64_t)blockIdx.y * kSiSlice, qe = min(c1, qs + kSiSlice);
+  if (split > 1 && qe > qs) {
+    const int64_t z0 = s.loff[qs], len = s.loff[qe] - z0;
+    const double* p = s.P + s.lpo[qs];
     for (int64_t idx = threadIdx.x; idx < len; idx += blockDim.x) {
       double v = p[idx];
       for (int t = 1; t < split; ++t) v += p[(int64_t)t * E + idx];
@@ -372,13 +383,15 @@ __global__ void __launch_bounds__(kSiWarps * 32) si_diag_kernel(SiDev s, const i
   const double* Dinv = s.L + s.loff[c0];
   double* Zkk = s.Z + s.loff[c0];
   const int ne = bk * bk;
+  const int64_t qst = (int64_t)s.maxb * s.maxb;                             // slice stride in Q
+  double* mine = Q + ((int64_t)blockIdx.x * slices + blockIdx.y) * qst;      // this slice's sum
   for (int e0 = 0; e0 < ne; e0 += kSiTileEnt) {
     int rr[kSiEnt], cc[kSiEnt];
     si_entries(e0, ne, bk, lane, rr, cc);
     double acc[kSiEnt];
 #pragma unroll
     for (int m = 0; m < kSiEnt; ++m) acc[m] = 0.0;
-    for (int64_t q = c0 + 1 + w; q < c1; q += kSiWarps) {
+    for (int64_t q = qs + w; q < qe; q += kSiWarps) {
       const int bj = s.bs[s.colrow[q]];
       const double* Zq = s.Z + s.loff[q];  // bj x bk
       const double* Lq = s.L + s.loff[q];
@@ -397,10 +410,26 @@ __global__ void __launch_bounds__(kSiWarps * 32) si_diag_kernel(SiDev s, const i
     for (int idx = threadIdx.x; idx < kSiTileEnt && e0 + idx < ne; idx += blockDim.x) {
       double v = red[idx];
       for (int t = 1; t < kSiWarps; ++t) v += red[t * kSiTileEnt + idx];
-      Zkk[e0 + idx] = Dinv[e0 + idx] - v;
+      if (slices == 1) Zkk[e0 + idx] = Dinv[e0 + idx] - v;
+      else mine[e0 + idx] = v;
     }
     __syncthreads();
   }
+  if (slices == 1) return;
+  // the last slice of this supernode adds all slices in order
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) last = atomicAdd(cnt + k, 1u) == (unsigned int)(slices - 1);
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  const double* all = Q + (int64_t)blockIdx.x * slices * qst;
+  for (int idx = threadIdx.x; idx < ne; idx += blockDim.x) {
+    double v = 0.0;
+    for (int t = 0; t < slices; ++t) v += ((volatile const double*)all)[(int64_t)t * qst + idx];
+    Zkk[idx] = Dinv[idx] - v;
+  }
+  if (threadIdx.x == 0) cnt[k] = 0u;
 }
 
 // out = alpha P_S(Z) + beta out: one warp per block of S
@@ -620,6 +649,8 @@ struct s_selinv_t {
   std::vector<int32_t> lvl_slices;  // pivot CTAs per supernode on each level
   std::vector<int64_t> lvl_ent;     // entries of the blocks of each level's columns
   std::vector<int32_t> upd_split, off_split;  // parts of the update and off-diagonal sums
+  unsigned int* cnt = nullptr;      // per supernode: slices of the diagonal kernel finished
+  double* Q = nullptr;              // slice sums of the diagonal kernel
   // device
   int32_t* bs = nullptr;
   int64_t* colptr = nullptr;
@@ -654,6 +685,8 @@ static void selinv_free(s_selinv_t* p) {
   cudaFree(p->aoff);
   cudaFree(p->lpo);
   cudaFree(p->P);
+  cudaFree(p->cnt);
+  cudaFree(p->Q);
   cudaFree(p->upd);
   cudaFree(p->off);
   cudaFree(p->sn);
@@ -784,7 +817,7 @@ static s_status selinv_build(s_selinv_t* p) {
   p->upd_split.assign(H, 1);
   p->off_split.assign(H, 1);
   const int64_t target = 2LL * kSiWarps * sm_count();  // two warps per SM sub-partition
-  int64_t scratch = 0;
+  int64_t scratch = 0, qneed = 0;
   for (int32_t l = 0; l < H; ++l) {
     int64_t longest = 0, ent = 0, maxrow = 0;
     const int64_t u0 = (int64_t)upd.size(), o0 = (int64_t)off.size();
@@ -815,6 +848,8 @@ static s_status selinv_build(s_selinv_t* p) {
     if (sp > 1) scratch = std::max<int64_t>(scratch, (int64_t)sp * ent);
     p->lvl_ent[l] = ent;
     p->lvl_slices[l] = (int32_t)std::max<int64_t>(1, (longest + kSiSlice - 1) / kSiSlice);
+    if (p->lvl_slices[l] > 1)
+      qneed = std::max<int64_t>(qneed, (int64_t)bylvl[l].size() * p->lvl_slices[l] * p->maxb * p->maxb);
     p->upd_ptr.push_back((int64_t)upd.size());
     p->off_ptr.push_back((int64_t)off.size());
     p->sn_ptr.push_back((int64_t)sn.size());
@@ -831,6 +866,9 @@ static s_status selinv_build(s_selinv_t* p) {
   if (ce == cudaSuccess) ce = cudaMalloc(&p->L, vb);
   if (ce == cudaSuccess) ce = cudaMalloc(&p->Z, vb);
   if (ce == cudaSuccess && scratch > 0) ce = cudaMalloc(&p->P, sizeof(double) * (size_t)scratch);
+  if (ce == cudaSuccess && qneed > 0) ce = cudaMalloc(&p->Q, sizeof(double) * (size_t)qneed);
+  if (ce == cudaSuccess) ce = cudaMalloc(&p->cnt, sizeof(unsigned int) * (size_t)std::max(m, 1));
+  if (ce == cudaSuccess) ce = cudaMemset(p->cnt, 0, sizeof(unsigned int) * (size_t)std::max(m, 1));
   if (ce == cudaErrorMemoryAllocation) {
     cudaGetLastError();
     return set_error(S_ERR_NOMEM, "selected inversion: no device memory for the factor");
@@ -946,6 +984,7 @@ s_status s_selinv_invert(s_selinv p, double alpha, double beta, double* out, voi
     if ((st = set_smem((const void*)si_offdiag_kernel, stage_bytes(p))) ||
         (st = set_smem((const void*)si_diag_kernel, diag_bytes(p))))
       return st;
+    SF_CUDA(cudaMemsetAsync(p->cnt, 0, sizeof(unsigned int) * (size_t)p->m, cs));
     for (int32_t l = p->height - 1; l >= 0; --l) {
       const int64_t n = p->off_ptr[l + 1] - p->off_ptr[l];
       const int split = n > 0 ? p->off_split[l] : 1;
@@ -955,9 +994,11 @@ s_status s_selinv_invert(s_selinv p, double alpha, double beta, double* out, voi
                                                                                  split, p->lvl_ent[l]);
       }
       const int64_t ns = p->sn_ptr[l + 1] - p->sn_ptr[l];
-      if (ns > 0)
-        si_diag_kernel<<<(unsigned)ns, kSiWarps * 32, diag_bytes(p), cs>>>(s, p->sn + p->sn_ptr[l], split,
-                                                                            p->lvl_ent[l]);
+      if (ns > 0) {
+        dim3 g((unsigned)ns, (unsigned)p->lvl_slices[l]);
+        si_diag_kernel<<<g, kSiWarps * 32, diag_bytes(p), cs>>>(s, p->sn + p->sn_ptr[l], split, p->lvl_ent[l],
+                                                                p->lvl_slices[l], p->cnt, p->Q);
+      }
     }
   }
   const DevPattern& d = p->S->d;
