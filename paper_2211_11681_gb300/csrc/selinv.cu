@@ -22,14 +22,17 @@
 //             supernode, its warps splitting the sum);
 //   scatter   out = alpha P_S(Z) + beta out, blocks of S read from Z or its transpose.
 //
-// The update and off-diagonal steps give one warp an output block (512-entry tiles of it,
-// 16 entries per lane) and a share of its sum: near the root the elimination tree is a
-// chain whose levels hold few, long sums, so the host splits each sum into `split` strided
-// parts (split-K) to keep every SM sub-partition busy.  With split > 1 the parts land in a
-// scratch buffer and the next launch of the level (pivot, diag) adds them in a fixed order,
-// so results do not depend on scheduling.  The operand blocks of each term are staged in
-// shared memory 16 columns at a time with coalesced loads (row pitch 17 doubles: rows fall
-// in different banks), so a warp waits for one L2 round trip per slice, not per product.
+// The terms of every sum are fixed by the pattern of L, so the plan lists them once (the
+// symbolic phase of both sweeps): per block of L the pairs (W(i,j), L(k,j)) of the update and
+// (Z(i,j), L(j,k)) of the inversion.  The update and off-diagonal steps give one warp an
+// output block (512-entry tiles of it, 16 entries per lane) and a contiguous part of its
+// term list: near the root the elimination tree is a chain whose levels hold few, long sums,
+// so the host splits each list into `split` parts (split-K) to keep every SM sub-partition
+// busy.  With split > 1 the parts land in a scratch buffer and the next launch of the level
+// (pivot, diag) adds them in a fixed order, so results do not depend on scheduling.  The
+// operand blocks of each term are staged in shared memory 16 columns at a time (row pitch 17
+// doubles: rows fall in different banks) by cp.async into one of two buffers per warp, the
+// next unit's copies in flight while the current unit is multiplied.
 //
 // Every entry a launch reads was written by an earlier launch (descendants sit on lower
 // levels, ancestors on higher ones) or by its own CTA before a barrier, so the kernels need
@@ -54,6 +57,7 @@ constexpr int kSiSlice = 8;               // column blocks per pivot CTA
 constexpr int kSiU = 16;                  // columns of t staged per slice
 constexpr int kSiUp = kSiU + 1;           // row pitch of a staged slice (doubles)
 constexpr int kSiMaxSplit = 16;           // parts of one split sum
+constexpr int kSiPartTerms = 8;           // fewest terms of one part
 constexpr int kSiMaxClusters = 32768;     // non-empty clusters of the host bitset analysis
 
 struct SiItem {
@@ -68,9 +72,13 @@ struct SiDev {
   const int32_t* colrow;  //   the diagonal first, then the rows of struct(k) ascending
   const int64_t* loff;    // entry offset of each CSC block (rows x cols, row-major)
   const int64_t* lpo;     // entry offset of each CSC block among the blocks of its level
-  const int64_t* rowptr;  // CSR of L: row i holds columns ascending, the diagonal last
-  const int32_t* rowcol;
-  const int32_t* rowblk;  // CSC block of each CSR entry
+  const int32_t* colcol;  // column position of each CSC block
+  const int64_t* uptr;    // factor terms of CSC block q: uptr[q] .. uptr[q+1]-1, pairs of
+  const int32_t* uw;      //   CSC blocks W(i,j), L(k,j)
+  const int32_t* ul;
+  const int64_t* optr;    // inversion terms of CSC block q = (i,k), i > k: for every j in
+  const int32_t* oz;      //   struct(k) the block of Z(i,j) (~index: stored as Z(j,i)) and
+  const int32_t* ol;      //   the block L(j,k)
   const int64_t* aoff;    // per CSC block: entry offset of the S block with its rows and
                           // columns (-1: not in S)
   double* W;              // L D (D in the diagonal blocks)
@@ -80,15 +88,6 @@ struct SiDev {
   unsigned int* flag;     // mapped host word: 1 = a pivot block was not positive definite
   int maxb;               // widest block of the plan
 };
-
-__device__ __forceinline__ int64_t si_lower_bound(const int32_t* a, int64_t lo, int64_t hi, int32_t v) {
-  while (lo < hi) {
-    const int64_t mid = (lo + hi) >> 1;
-    if (__ldg(a + mid) < v) lo = mid + 1;
-    else hi = mid;
-  }
-  return lo;
-}
 
 // Entry coordinates of a lane's kSiEnt entries of a rows x cols tile starting at e0.
 __device__ __forceinline__ void si_entries(int e0, int ne, int cols, int lane, int* rr, int* cc) {
@@ -137,8 +136,36 @@ __device__ __forceinline__ void si_stage(double* dst, const double* src, int row
   }
 }
 
-// factor update: W(i,k) = A(i,k) + sigma [i = k] - sum_j W(i,j) L(k,j)^T; warp gw serves
-// item gw / split and the part gw % split of its sum (32-candidate chunks of row k).
+// Asynchronous 8-byte copy global -> shared (cp.async, zero fill when !valid; src must still
+// point into the buffer), and its group commit / wait.
+__device__ __forceinline__ void si_cp8(double* dst, const double* src, bool valid) {
+  const uint32_t d = (uint32_t)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(d), "l"(src), "r"(valid ? 8 : 0) : "memory");
+}
+__device__ __forceinline__ void si_cp_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void si_cp_wait1() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
+__device__ __forceinline__ void si_cp_wait0() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+
+// si_stage with cp.async: the copies complete at the lane's next wait on their group.
+__device__ __forceinline__ void si_stage_async(double* dst, const double* src, int rows, int uw, int uw4, int rs,
+                                               int ts, int lane) {
+  if (ts == 1) {
+    for (int idx = lane; idx < rows * uw4; idx += 32) {
+      const int r = idx / uw4, t = idx - r * uw4;
+      si_cp8(dst + r * kSiUp + t, t < uw ? src + (int64_t)r * rs + t : src, t < uw);
+    }
+  } else {
+    for (int idx = lane; idx < rows * uw4; idx += 32) {
+      const int t = idx / rows, r = idx - t * rows;
+      si_cp8(dst + r * kSiUp + t, t < uw ? src + (int64_t)t * ts + (int64_t)r * rs : src, t < uw);
+    }
+  }
+}
+
+// factor update: W(i,k) = A(i,k) + sigma [i = k] - sum_j W(i,j) L(k,j)^T over the block's term
+// list; warp gw serves item gw / split and the part gw % split of the list.  The term list
+// is walked in units of one term and 16 columns of t; the next unit's blocks are copied into
+// the warp's second stage buffer (cp.async) while the current unit is multiplied.
 __global__ void __launch_bounds__(kSiWarps * 32) si_update_kernel(SiDev s, const SiItem* __restrict__ items,
                                                                    int64_t nitems, int split, int64_t E,
                                                                    const double* __restrict__ A, double sigma) {
@@ -152,8 +179,8 @@ __global__ void __launch_bounds__(kSiWarps * 32) si_update_kernel(SiDev s, const
   const int i = s.colrow[it.blk], k = it.col;
   const int bi = s.bs[i], bk = s.bs[k];
   const int ne = bi * bk;
-  double* sa = sh + (size_t)w * 2 * s.maxb * kSiUp;
-  double* sb = sa + (size_t)s.maxb * kSiUp;
+  const size_t half = (size_t)2 * s.maxb * kSiUp;       // one stage buffer: operand a | operand b
+  double* buf = sh + (size_t)w * 2 * half;
   int rr[kSiEnt], cc[kSiEnt];
   si_entries(it.e0, ne, bk, lane, rr, cc);
   double acc[kSiEnt];
@@ -167,41 +194,40 @@ __global__ void __launch_bounds__(kSiWarps * 32) si_update_kernel(SiDev s, const
     }
     acc[m] = v;
   }
-  // j < k in both row i and row k of L: candidates from the shorter list (row k below its
-  // diagonal, or row i below column k), matched by binary search in the other
-  const int64_t rk0 = s.rowptr[k], rk1 = s.rowptr[k + 1] - 1;
-  const int64_t ri0 = s.rowptr[i];
-  const int64_t ri1 = i == k ? rk1 : si_lower_bound(s.rowcol, ri0, s.rowptr[i + 1], k);
-  const bool from_k = rk1 - rk0 <= ri1 - ri0;
-  const int64_t c0 = from_k ? rk0 : ri0, c1 = from_k ? rk1 : ri1;  // candidates
-  const int64_t m1 = from_k ? ri1 : rk1;                           // searched list [lo, m1)
-  int64_t lo = from_k ? ri0 : rk0;
-  for (int64_t base = c0 + 32 * (int64_t)part; base < c1; base += 32 * (int64_t)split) {
-    const int64_t q = base + lane;
-    const int32_t j = q < c1 ? __ldg(s.rowcol + q) : INT32_MAX;
-    const int64_t a = si_lower_bound(s.rowcol, lo, m1, j);
-    const bool hit = q < c1 && a < m1 && __ldg(s.rowcol + a) == j;
-    const int bij = hit ? __ldg(s.rowblk + (from_k ? a : q)) : 0;
-    const int bkj = hit ? __ldg(s.rowblk + (from_k ? q : a)) : 0;
-    unsigned int mask = __ballot_sync(0xffffffffu, hit);
-    lo = __shfl_sync(0xffffffffu, a, 31);
-    while (mask) {
-      const int src = __ffs(mask) - 1;
-      mask &= mask - 1u;
-      const int jj = __shfl_sync(0xffffffffu, j, src);
-      const double* Wij = s.W + s.loff[__shfl_sync(0xffffffffu, bij, src)];  // bi x bj
-      const double* Lkj = s.L + s.loff[__shfl_sync(0xffffffffu, bkj, src)];  // bk x bj
-      const int bj = s.bs[jj];
-      for (int u0 = 0; u0 < bj; u0 += kSiU) {
-        const int uw = min(kSiU, bj - u0), uw4 = (uw + 3) & ~3;
-        __syncwarp();
-        si_stage(sa, Wij + u0, bi, uw, uw4, bj, 1, lane);
-        si_stage(sb, Lkj + u0, bk, uw, uw4, bj, 1, lane);
-        __syncwarp();
-        si_dot(sa, sb, uw4, rr, cc, -1.0, acc);
-      }
+  const int64_t t0 = s.uptr[it.blk], nt = s.uptr[it.blk + 1] - t0;
+  int64_t t = t0 + nt * part / split;
+  const int64_t te = t0 + nt * (part + 1) / split;
+  auto issue = [&](int64_t tt, int u0, double* dst) {
+    const int bw = s.uw[tt], bl = s.ul[tt];
+    const int bj = s.bs[s.colcol[bw]];
+    const int uw = min(kSiU, bj - u0), uw4 = (uw + 3) & ~3;
+    si_stage_async(dst, s.W + s.loff[bw] + u0, bi, uw, uw4, bj, 1, lane);             // W(i,j)
+    si_stage_async(dst + s.maxb * kSiUp, s.L + s.loff[bl] + u0, bk, uw, uw4, bj, 1, lane);  // L(k,j)
+  };
+  int u0 = 0, cur = 0;
+  if (t < te) issue(t, 0, buf);
+  si_cp_commit();
+  while (t < te) {
+    const int bj = s.bs[s.colcol[s.uw[t]]];
+    const int uw4 = (min(kSiU, bj - u0) + 3) & ~3;
+    int64_t tn = t;
+    int un = u0 + kSiU;
+    if (un >= bj) {
+      tn = t + 1;
+      un = 0;
     }
+    if (tn < te) issue(tn, un, buf + (cur ^ 1) * half);
+    si_cp_commit();
+    si_cp_wait1();
+    __syncwarp();
+    const double* cb = buf + cur * half;
+    si_dot(cb, cb + s.maxb * kSiUp, uw4, rr, cc, -1.0, acc);
+    __syncwarp();
+    t = tn;
+    u0 = un;
+    cur ^= 1;
   }
+  si_cp_wait0();
   double* out = split > 1 ? s.P + (int64_t)part * E + s.lpo[it.blk] : s.W + s.loff[it.blk];
 #pragma unroll
   for (int m = 0; m < kSiEnt; ++m)
@@ -289,8 +315,9 @@ __global__ void __launch_bounds__(kSiThreads) si_pivot_kernel(SiDev s, const int
   }
 }
 
-// inversion, off-diagonal blocks: Z(i,k) = - sum_{j in struct(k)} Z(i,j) L(j,k); warp gw
-// serves item gw / split and the part gw % split of struct(k) (32-entry chunks).
+// inversion, off-diagonal blocks: Z(i,k) = - sum_{j in struct(k)} Z(i,j) L(j,k) over the block's
+// term list; warp gw serves item gw / split and the part gw % split of the list, staged and
+// prefetched as in the update.
 __global__ void __launch_bounds__(kSiWarps * 32) si_offdiag_kernel(SiDev s, const SiItem* __restrict__ items,
                                                                     int64_t nitems, int split, int64_t E) {
   extern __shared__ double sh[];
@@ -303,48 +330,50 @@ __global__ void __launch_bounds__(kSiWarps * 32) si_offdiag_kernel(SiDev s, cons
   const int i = s.colrow[it.blk], k = it.col;
   const int bi = s.bs[i], bk = s.bs[k];
   const int ne = bi * bk;
-  double* sa = sh + (size_t)w * 2 * s.maxb * kSiUp;
-  double* sb = sa + (size_t)s.maxb * kSiUp;
+  const size_t half = (size_t)2 * s.maxb * kSiUp;
+  double* buf = sh + (size_t)w * 2 * half;
   int rr[kSiEnt], cc[kSiEnt];
   si_entries(it.e0, ne, bk, lane, rr, cc);
   double acc[kSiEnt];
 #pragma unroll
   for (int m = 0; m < kSiEnt; ++m) acc[m] = 0.0;
-  const int64_t q0 = s.colptr[k] + 1, q1 = s.colptr[k + 1];
-  for (int64_t base = q0 + 32 * (int64_t)part; base < q1; base += 32 * (int64_t)split) {
-    const int64_t q = base + lane;
-    const bool valid = q < q1;
-    const int j = valid ? __ldg(s.colrow + q) : 0;
-    // block (max(i,j), min(i,j)) of Z: row max in the CSC column min
-    const int hi = max(i, j), lw = min(i, j);
-    int zb = -1;
-    if (valid) {
-      const int64_t a0 = s.colptr[lw], a1 = s.colptr[lw + 1];
-      const int64_t a = si_lower_bound(s.colrow, a0, a1, hi);
-      if (a < a1 && __ldg(s.colrow + a) == hi) zb = (int)a;
+  const int64_t t0 = s.optr[it.blk], nt = s.optr[it.blk + 1] - t0;
+  int64_t t = t0 + nt * part / split;
+  const int64_t te = t0 + nt * (part + 1) / split;
+  auto issue = [&](int64_t tt, int u0, double* dst) {
+    const int zb = s.oz[tt], qq = s.ol[tt];
+    const int bj = s.bs[s.colrow[qq]];
+    const int uw = min(kSiU, bj - u0), uw4 = (uw + 3) & ~3;
+    if (zb < 0)  // Z(i,j) = Z(j,i)^T, block bj x bi
+      si_stage_async(dst, s.Z + s.loff[~zb] + (int64_t)u0 * bi, bi, uw, uw4, 1, bi, lane);
+    else
+      si_stage_async(dst, s.Z + s.loff[zb] + u0, bi, uw, uw4, bj, 1, lane);
+    si_stage_async(dst + s.maxb * kSiUp, s.L + s.loff[qq] + (int64_t)u0 * bk, bk, uw, uw4, 1, bk, lane);  // L(j,k)
+  };
+  int u0 = 0, cur = 0;
+  if (t < te) issue(t, 0, buf);
+  si_cp_commit();
+  while (t < te) {
+    const int bj = s.bs[s.colrow[s.ol[t]]];
+    const int uw4 = (min(kSiU, bj - u0) + 3) & ~3;
+    int64_t tn = t;
+    int un = u0 + kSiU;
+    if (un >= bj) {
+      tn = t + 1;
+      un = 0;
     }
-    unsigned int mask = __ballot_sync(0xffffffffu, zb >= 0);
-    while (mask) {
-      const int src = __ffs(mask) - 1;
-      mask &= mask - 1u;
-      const int jj = __shfl_sync(0xffffffffu, j, src);
-      const int zz = __shfl_sync(0xffffffffu, zb, src);
-      const int64_t qq = base + src;
-      const int bj = s.bs[jj];
-      const bool tr = i < jj;                    // Z(i,j) = Z(j,i)^T
-      const double* Zp = s.Z + s.loff[zz];       // bi x bj, or bj x bi when tr
-      const double* Ljk = s.L + s.loff[qq];      // bj x bk
-      for (int u0 = 0; u0 < bj; u0 += kSiU) {
-        const int uw = min(kSiU, bj - u0), uw4 = (uw + 3) & ~3;
-        __syncwarp();
-        if (tr) si_stage(sa, Zp + (int64_t)u0 * bi, bi, uw, uw4, 1, bi, lane);
-        else si_stage(sa, Zp + u0, bi, uw, uw4, bj, 1, lane);
-        si_stage(sb, Ljk + (int64_t)u0 * bk, bk, uw, uw4, 1, bk, lane);
-        __syncwarp();
-        si_dot(sa, sb, uw4, rr, cc, -1.0, acc);
-      }
-    }
+    if (tn < te) issue(tn, un, buf + (cur ^ 1) * half);
+    si_cp_commit();
+    si_cp_wait1();
+    __syncwarp();
+    const double* cb = buf + cur * half;
+    si_dot(cb, cb + s.maxb * kSiUp, uw4, rr, cc, -1.0, acc);
+    __syncwarp();
+    t = tn;
+    u0 = un;
+    cur ^= 1;
   }
+  si_cp_wait0();
   double* out = split > 1 ? s.P + (int64_t)part * E + s.lpo[it.blk] : s.Z + s.loff[it.blk];
 #pragma unroll
   for (int m = 0; m < kSiEnt; ++m)
@@ -642,7 +671,7 @@ using namespace sf;
 struct s_selinv_t {
   const s_pattern_t* S = nullptr;
   int32_t m = 0, height = 0, maxb = 0;
-  int64_t nl = 0, nent = 0;
+  int64_t nl = 0, nent = 0, nterms = 0;
   double flops_factor = 0.0, flops_invert = 0.0;
   // level lists (host offsets into the device arrays)
   std::vector<int64_t> upd_ptr, off_ptr, sn_ptr;
@@ -656,9 +685,13 @@ struct s_selinv_t {
   int64_t* colptr = nullptr;
   int32_t* colrow = nullptr;
   int64_t* loff = nullptr;
-  int64_t* rowptr = nullptr;
-  int32_t* rowcol = nullptr;
-  int32_t* rowblk = nullptr;
+  int32_t* colcol = nullptr;
+  int64_t* uptr = nullptr;
+  int32_t* uw = nullptr;
+  int32_t* ul = nullptr;
+  int64_t* optr = nullptr;
+  int32_t* oz = nullptr;
+  int32_t* ol = nullptr;
   int64_t* aoff = nullptr;
   int64_t* lpo = nullptr;
   double* P = nullptr;
@@ -679,9 +712,13 @@ static void selinv_free(s_selinv_t* p) {
   cudaFree(p->colptr);
   cudaFree(p->colrow);
   cudaFree(p->loff);
-  cudaFree(p->rowptr);
-  cudaFree(p->rowcol);
-  cudaFree(p->rowblk);
+  cudaFree(p->colcol);
+  cudaFree(p->uptr);
+  cudaFree(p->uw);
+  cudaFree(p->ul);
+  cudaFree(p->optr);
+  cudaFree(p->oz);
+  cudaFree(p->ol);
   cudaFree(p->aoff);
   cudaFree(p->lpo);
   cudaFree(p->P);
@@ -704,9 +741,13 @@ static SiDev dev_of(const s_selinv_t* p) {
   s.colptr = p->colptr;
   s.colrow = p->colrow;
   s.loff = p->loff;
-  s.rowptr = p->rowptr;
-  s.rowcol = p->rowcol;
-  s.rowblk = p->rowblk;
+  s.colcol = p->colcol;
+  s.uptr = p->uptr;
+  s.uw = p->uw;
+  s.ul = p->ul;
+  s.optr = p->optr;
+  s.oz = p->oz;
+  s.ol = p->ol;
   s.aoff = p->aoff;
   s.lpo = p->lpo;
   s.W = p->W;
@@ -802,6 +843,55 @@ static s_status selinv_build(s_selinv_t* p) {
   }
   for (int32_t k = 0; k < m; ++k)
     if (aoff[colptr[k]] < 0) return set_error(S_ERR_PATTERN, "selected inversion: pattern lacks a diagonal block");
+  // Term lists of both sweeps (fixed by the pattern of L), per CSC block q = (i,k):
+  //   factor:    the j < k in both row i and row k of L, as CSC blocks W(i,j), L(k,j);
+  //   inversion: (i > k) for every j in struct(k), the block holding Z(i,j) (~index when it is
+  //              stored as Z(j,i)) and the block L(j,k).
+  std::vector<int64_t> uptr(nl + 1, 0), optr(nl + 1, 0);
+  std::vector<int32_t> uw, ul, oz, ol, colcol(nl);
+  for (int32_t k = 0; k < m; ++k) {
+    const int64_t rk0 = rowptr[k], rk1 = rowptr[k + 1] - 1;  // row k below its diagonal
+    for (int64_t q = colptr[k]; q < colptr[k + 1]; ++q) {
+      const int32_t i = colrow[q];
+      colcol[q] = k;
+      for (int64_t a = rowptr[i], ae = rowptr[i + 1], b = rk0; a < ae && b < rk1 && rowcol[a] < k;) {
+        if (rowcol[a] < rowcol[b]) {
+          ++a;
+        } else if (rowcol[b] < rowcol[a]) {
+          ++b;
+        } else {
+          uw.push_back(rowblk[a]);
+          ul.push_back(rowblk[b]);
+          ++a;
+          ++b;
+        }
+      }
+      uptr[q + 1] = (int64_t)uw.size();
+      if (q > colptr[k]) {
+        int64_t ra = rowptr[i], ca = colptr[i] + 1;
+        const int64_t re = rowptr[i + 1], ce = colptr[i + 1];
+        for (int64_t qq = colptr[k] + 1; qq < colptr[k + 1]; ++qq) {
+          const int32_t j = colrow[qq];
+          int32_t zb;
+          if (j < i) {
+            while (ra < re && rowcol[ra] < j) ++ra;
+            if (ra == re || rowcol[ra] != j) return set_error(S_ERR_PATTERN, "selected inversion: internal error");
+            zb = rowblk[ra];
+          } else if (j == i) {
+            zb = (int32_t)colptr[i];
+          } else {
+            while (ca < ce && colrow[ca] < j) ++ca;
+            if (ca == ce || colrow[ca] != j) return set_error(S_ERR_PATTERN, "selected inversion: internal error");
+            zb = ~(int32_t)ca;
+          }
+          oz.push_back(zb);
+          ol.push_back((int32_t)qq);
+        }
+      }
+      optr[q + 1] = (int64_t)oz.size();
+    }
+  }
+  p->nterms = (int64_t)uw.size() + (int64_t)oz.size();
   // level lists, level-local entry offsets, and the split of each level's long sums
   const int32_t H = p->height;
   std::vector<std::vector<int32_t>> bylvl(H);
@@ -819,13 +909,14 @@ static s_status selinv_build(s_selinv_t* p) {
   const int64_t target = 2LL * kSiWarps * sm_count();  // two warps per SM sub-partition
   int64_t scratch = 0, qneed = 0;
   for (int32_t l = 0; l < H; ++l) {
-    int64_t longest = 0, ent = 0, maxrow = 0;
+    int64_t longest = 0, ent = 0, maxu = 0, maxo = 0;
     const int64_t u0 = (int64_t)upd.size(), o0 = (int64_t)off.size();
     for (int32_t k : bylvl[l]) {
       sn.push_back(k);
       longest = std::max<int64_t>(longest, colptr[k + 1] - colptr[k] - 1);
-      maxrow = std::max<int64_t>(maxrow, rowptr[k + 1] - rowptr[k] - 1);
       for (int64_t q = colptr[k]; q < colptr[k + 1]; ++q) {
+        maxu = std::max<int64_t>(maxu, uptr[q + 1] - uptr[q]);
+        maxo = std::max<int64_t>(maxo, optr[q + 1] - optr[q]);
         const int ne = bs[colrow[q]] * bs[k];
         lpo[q] = ent;
         ent += ne;
@@ -836,14 +927,14 @@ static s_status selinv_build(s_selinv_t* p) {
       }
     }
     const int64_t nu = (int64_t)upd.size() - u0, no = (int64_t)off.size() - o0;
-    auto choose = [&](int64_t items, int64_t len) {
+    auto choose = [&](int64_t items, int64_t terms) {  // parts of at least kSiPartTerms terms
       int64_t sp = items > 0 ? (target + items - 1) / items : 1;
-      sp = std::min<int64_t>(sp, std::min<int64_t>(kSiMaxSplit, (len + 31) / 32));
+      sp = std::min<int64_t>(sp, std::min<int64_t>(kSiMaxSplit, (terms + kSiPartTerms - 1) / kSiPartTerms));
       while (sp > 1 && sp * ent > (int64_t)1 << 27) --sp;  // scratch at most 1 GiB
       return (int32_t)std::max<int64_t>(1, sp);
     };
-    p->upd_split[l] = choose(nu, maxrow);
-    p->off_split[l] = choose(no, longest);
+    p->upd_split[l] = choose(nu, maxu);
+    p->off_split[l] = choose(no, maxo);
     const int32_t sp = std::max(p->upd_split[l], p->off_split[l]);
     if (sp > 1) scratch = std::max<int64_t>(scratch, (int64_t)sp * ent);
     p->lvl_ent[l] = ent;
@@ -855,8 +946,10 @@ static s_status selinv_build(s_selinv_t* p) {
     p->sn_ptr.push_back((int64_t)sn.size());
   }
   if ((st = upload(&p->bs, bs)) || (st = upload(&p->colptr, colptr)) || (st = upload(&p->colrow, colrow)) ||
-      (st = upload(&p->loff, loff)) || (st = upload(&p->rowptr, rowptr)) || (st = upload(&p->rowcol, rowcol)) ||
-      (st = upload(&p->rowblk, rowblk)) || (st = upload(&p->aoff, aoff)) || (st = upload(&p->lpo, lpo)) ||
+      (st = upload(&p->loff, loff)) || (st = upload(&p->colcol, colcol)) || (st = upload(&p->uptr, uptr)) ||
+      (st = upload(&p->uw, uw)) || (st = upload(&p->ul, ul)) || (st = upload(&p->optr, optr)) ||
+      (st = upload(&p->oz, oz)) || (st = upload(&p->ol, ol)) || (st = upload(&p->aoff, aoff)) ||
+      (st = upload(&p->lpo, lpo)) ||
       (st = upload(&p->upd, upd)) ||
       (st = upload(&p->off, off)) || (st = upload(&p->sn, sn)) || (st = upload(&p->s2l, s2l)) ||
       (st = upload(&p->s2t, s2t)))
@@ -936,9 +1029,11 @@ s_status s_selinv_stats(s_selinv p, int64_t* l_blocks, int64_t* l_entries, int32
 
 // Dynamic shared memory of the block kernels (per-warp staging of two operand slices, and
 // the diagonal kernel's warp sums) and of the pivot kernel (D^{-1} and one W block).
-static size_t stage_bytes(const s_selinv_t* p) { return sizeof(double) * (size_t)kSiWarps * 2 * p->maxb * kSiUp; }
-static size_t diag_bytes(const s_selinv_t* p) {
-  return stage_bytes(p) + sizeof(double) * (size_t)kSiWarps * kSiTileEnt;
+static size_t stage_bytes(const s_selinv_t* p) {  // two stage buffers per warp
+  return sizeof(double) * (size_t)kSiWarps * 4 * p->maxb * kSiUp;
+}
+static size_t diag_bytes(const s_selinv_t* p) {  // one stage buffer per warp and the warp sums
+  return sizeof(double) * ((size_t)kSiWarps * 2 * p->maxb * kSiUp + (size_t)kSiWarps * kSiTileEnt);
 }
 static size_t pivot_bytes(const s_selinv_t* p) { return sizeof(double) * 2 * (size_t)p->maxb * p->maxb; }
 
