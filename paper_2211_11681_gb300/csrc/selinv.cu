@@ -99,8 +99,8 @@ __device__ __forceinline__ void si_entries(int e0, int ne, int cols, int lane, i
   }
 }
 
-// acc[m] += sign * sum_t a[rr[m]][t] b[cc[m]][t] over t < uw4 (staged, zero padded to 4).
-__device__ __forceinline__ void si_dot(const double* a, const double* b, int uw4, const int* rr, const int* cc,
+// acc[m] += sign * sum_t a[rr[m]][t] b[cc[m]][t] over t < uw (staged slices).
+__device__ __forceinline__ void si_dot(const double* a, const double* b, int uw, const int* rr, const int* cc,
                                        double sign, double* acc) {
 #pragma unroll
   for (int m = 0; m < kSiEnt; ++m) {
@@ -108,12 +108,14 @@ __device__ __forceinline__ void si_dot(const double* a, const double* b, int uw4
     const double* ar = a + rr[m] * kSiUp;
     const double* br = b + cc[m] * kSiUp;
     double t0 = 0.0, t1 = 0.0;
-    for (int t = 0; t < uw4; t += 4) {
+    int t = 0;
+    for (; t + 4 <= uw; t += 4) {
       t0 = fma(ar[t], br[t], t0);
       t1 = fma(ar[t + 1], br[t + 1], t1);
       t0 = fma(ar[t + 2], br[t + 2], t0);
       t1 = fma(ar[t + 3], br[t + 3], t1);
     }
+    for (; t < uw; ++t) t0 = fma(ar[t], br[t], t0);
     acc[m] = fma(sign, t0 + t1, acc[m]);
   }
 }
@@ -209,7 +211,7 @@ __global__ void __launch_bounds__(kSiWarps * 32) si_update_kernel(SiDev s, const
   si_cp_commit();
   while (t < te) {
     const int bj = s.bs[s.colcol[s.uw[t]]];
-    const int uw4 = (min(kSiU, bj - u0) + 3) & ~3;
+    const int uwc = min(kSiU, bj - u0);
     int64_t tn = t;
     int un = u0 + kSiU;
     if (un >= bj) {
@@ -221,7 +223,7 @@ __global__ void __launch_bounds__(kSiWarps * 32) si_update_kernel(SiDev s, const
     si_cp_wait1();
     __syncwarp();
     const double* cb = buf + cur * half;
-    si_dot(cb, cb + s.maxb * kSiUp, uw4, rr, cc, -1.0, acc);
+    si_dot(cb, cb + s.maxb * kSiUp, uwc, rr, cc, -1.0, acc);
     __syncwarp();
     t = tn;
     u0 = un;
@@ -355,7 +357,7 @@ __global__ void __launch_bounds__(kSiWarps * 32) si_offdiag_kernel(SiDev s, cons
   si_cp_commit();
   while (t < te) {
     const int bj = s.bs[s.colrow[s.ol[t]]];
-    const int uw4 = (min(kSiU, bj - u0) + 3) & ~3;
+    const int uwc = min(kSiU, bj - u0);
     int64_t tn = t;
     int un = u0 + kSiU;
     if (un >= bj) {
@@ -367,7 +369,7 @@ __global__ void __launch_bounds__(kSiWarps * 32) si_offdiag_kernel(SiDev s, cons
     si_cp_wait1();
     __syncwarp();
     const double* cb = buf + cur * half;
-    si_dot(cb, cb + s.maxb * kSiUp, uw4, rr, cc, -1.0, acc);
+    si_dot(cb, cb + s.maxb * kSiUp, uwc, rr, cc, -1.0, acc);
     __syncwarp();
     t = tn;
     u0 = un;
@@ -430,7 +432,7 @@ __global__ void __launch_bounds__(kSiWarps * 32) si_diag_kernel(SiDev s, const i
         si_stage(sa, Zq + (int64_t)u0 * bk, bk, uw, uw4, 1, bk, lane);
         si_stage(sb, Lq + (int64_t)u0 * bk, bk, uw, uw4, 1, bk, lane);
         __syncwarp();
-        si_dot(sa, sb, uw4, rr, cc, 1.0, acc);
+        si_dot(sa, sb, uw, rr, cc, 1.0, acc);
       }
     }
 #pragma unroll
