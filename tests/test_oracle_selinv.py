@@ -89,6 +89,21 @@ def test_block_inverse_formula():
     np.testing.assert_allclose(Z.to_dense(), want, rtol=1e-12, atol=1e-14)
 
 
+def test_inverse_columns_by_conjugate_gradients():
+    """Columns of the KMS inverse (closed form) through the sparse CG route, with a shift."""
+    bsize = np.array([3, 2, 4, 1, 3, 5])
+    n = int(bsize.sum())
+    rho = 0.6
+    A = BlockCSR.from_dense(kms(n, rho), bsize, *full_pattern(len(bsize)))
+    M = selinv.to_scipy(A)
+    np.testing.assert_array_equal(M.toarray(), kms(n, rho))
+    cols = [0, 5, n - 1]
+    X = selinv.inverse_columns(M, 0.0, cols)
+    np.testing.assert_allclose(X, kms_inverse(n, rho)[:, cols], rtol=0, atol=1e-10)
+    Xs = selinv.inverse_columns(M, 0.5, cols)
+    np.testing.assert_allclose(Xs, np.linalg.inv(kms(n, rho) + 0.5 * np.eye(n))[:, cols], rtol=0, atol=1e-10)
+
+
 def test_diagonal_shift():
     bsize = np.array([2, 3])
     d = np.array([1.0, 2.0, 4.0, 0.5, 3.0])
