@@ -40,6 +40,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <new>
 #include <vector>
 
 #include "common.cuh"
@@ -614,7 +615,13 @@ std::vector<int32_t> etree_levels(const Symbolic& sy, int32_t* height) {
 
 template <typename T>
 s_status upload(T** dst, const std::vector<T>& v) {
-  SF_CUDA(cudaMalloc((void**)dst, sizeof(T) * std::max<size_t>(v.size(), 1)));
+  const cudaError_t e = cudaMalloc((void**)dst, sizeof(T) * std::max<size_t>(v.size(), 1));
+  if (e == cudaErrorMemoryAllocation) {
+    cudaGetLastError();
+    *dst = nullptr;
+    return set_error(S_ERR_NOMEM, "selected inversion: no device memory for the plan's lists");
+  }
+  SF_CUDA(e);
   if (!v.empty()) SF_CUDA(cudaMemcpy(*dst, v.data(), sizeof(T) * v.size(), cudaMemcpyHostToDevice));
   return S_OK;
 }
@@ -985,7 +992,12 @@ s_status s_selinv_order(int32_t n_clusters, const int64_t* rowptr, const int32_t
   for (int32_t r = 0; r < n_clusters; ++r)
     if (rowptr[r + 1] < rowptr[r]) return set_error(S_ERR_PATTERN, "s_selinv_order: rowptr decreases");
   Symbolic sy;
-  s_status st = symbolic(n_clusters, rowptr, colidx, bsize, &sy);
+  s_status st;
+  try {
+    st = symbolic(n_clusters, rowptr, colidx, bsize, &sy);
+  } catch (const std::bad_alloc&) {
+    st = set_error(S_ERR_NOMEM, "s_selinv_order: host memory exhausted");
+  }
   if (st) return st;
   std::memcpy(perm, sy.perm.data(), sizeof(int32_t) * n_clusters);
   int64_t nl = sy.m;
@@ -1001,7 +1013,12 @@ s_status s_selinv_create(s_pattern S, s_selinv* out) {
   if (!S || !out) return set_error(S_ERR_ARG, "s_selinv_create: null argument");
   s_selinv_t* p = new s_selinv_t();
   p->S = S;
-  s_status st = selinv_build(p);
+  s_status st;
+  try {
+    st = selinv_build(p);
+  } catch (const std::bad_alloc&) {
+    st = set_error(S_ERR_NOMEM, "selected inversion: host memory exhausted in the symbolic analysis");
+  }
   if (st) {
     selinv_free(p);
     delete p;
