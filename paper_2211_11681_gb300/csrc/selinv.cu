@@ -57,7 +57,7 @@ constexpr int kSiThreads = 128;           // threads of the pivot and diagonal k
 constexpr int kSiSlice = 8;               // column blocks per pivot CTA
 constexpr int kSiU = 16;                  // columns of t staged per slice
 constexpr int kSiUp = kSiU + 1;           // row pitch of a staged slice (doubles)
-constexpr int kSiMaxSplit = 32;           // parts of one split sum
+constexpr int kSiMaxSplit = 64;           // parts of one split sum
 constexpr int kSiPartTerms = 4;           // fewest terms of one part
 constexpr int kSiMaxClusters = 32768;     // non-empty clusters of the host bitset analysis
 
@@ -915,7 +915,7 @@ static s_status selinv_build(s_selinv_t* p) {
   p->lvl_ent.assign(H, 0);
   p->upd_split.assign(H, 1);
   p->off_split.assign(H, 1);
-  const int64_t target = 8LL * kSiWarps * sm_count();  // eight warps per SM sub-partition
+  const int64_t target = 16LL * kSiWarps * sm_count();  // sixteen warps per SM sub-partition
   int64_t scratch = 0, qneed = 0;
   for (int32_t l = 0; l < H; ++l) {
     int64_t longest = 0, ent = 0, maxu = 0, maxo = 0;
